@@ -1,0 +1,205 @@
+"""FP64 CPU oracle for the batched 1D-TDSE hot path (arXiv:2507.04115, Sec. 3.1 and 4.2).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  It shares no code with the CUDA path.
+
+Contents
+  * ctypes bindings of ``tdse_oracle.c`` (grid, mask, ground state, energy, propagation);
+  * ``spectrum``: |DFT(a)|^2 dt^2 with numpy's FFT as the library primitive (reading F:
+    plain FFT over the Nt+1 samples, no window; the paper warns that the periodic FFT makes
+    the dipole, current and acceleration forms differ, App. A, last paragraph);
+  * ``lowest_eigenvalue`` / ``fit_softening``: the soft-core parameter a such that the
+    ground-state energy of the discrete field-free Hamiltonian equals a target (Sec. 3.1,
+    the sentence after Eq. "SC potential"), by a bracketing root finder;
+  * ``propagate_many``: one oracle instance per worker process (spawned), for baselines.
+
+Scheme ids: 0 = FULL_CN (E in the diagonal at the midpoint field), 1 = NUMEROV_SPLIT
+(the paper's Eqs. "CN - step 4/2/3").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+FULL_CN = 0
+NUMEROV_SPLIT = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tdse_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_lp = ctypes.POINTER(ctypes.c_long)
+
+
+def build(force: bool = False) -> str:
+    """Compile tdse_oracle.c into oracle/_liboracle.so with gcc (plain -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.oracle_grid.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+        L.oracle_mask.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+        L.oracle_energy.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    _dp, _dp]
+        L.oracle_ground_state.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_double,
+                                          _dp, _dp, _lp]
+        L.oracle_propagate.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_long, ctypes.c_long,
+                                       _dp, _dp, _dp]
+        for f in (L.oracle_grid, L.oracle_mask, L.oracle_energy, L.oracle_ground_state, L.oracle_propagate):
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError("%s failed (rc=%d)" % (what, rc))
+
+
+def grid(N, dx, a, Z=1.0):
+    """x_j, V_j and dV/dx at x_j on the cell-centred grid (reading G)."""
+    x = np.empty(N); V = np.empty(N); dV = np.empty(N)
+    _check(lib().oracle_grid(N, dx, a, Z, _ptr(x), _ptr(V), _ptr(dV)), "oracle_grid")
+    return x, V, dV
+
+
+def mask(N, dx, width=20.0, exponent=0.125):
+    """cos^p edge mask (reading D); width <= 0 returns ones."""
+    m = np.empty(N)
+    _check(lib().oracle_mask(N, dx, width, exponent, _ptr(m)), "oracle_mask")
+    return m
+
+
+def energy(psi, dx, a, Z=1.0, scheme=FULL_CN):
+    """<psi|H0|psi>/<psi|psi> for the scheme's discrete field-free Hamiltonian."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    e = np.zeros(1)
+    _check(lib().oracle_energy(psi.size, dx, a, Z, scheme, psi.view(np.float64).ctypes.data_as(_dp), _ptr(e)),
+           "oracle_energy")
+    return float(e[0])
+
+
+def ground_state(N, dx, a, Z=1.0, scheme=FULL_CN, dtau=0.1, max_iter=20000, tol=1e-13):
+    """Imaginary-time Crank-Nicolson ground state (reading GS). Returns (psi, E, iterations)."""
+    psi = np.zeros(N, dtype=np.complex128)
+    e = np.zeros(1)
+    it = ctypes.c_long(0)
+    _check(lib().oracle_ground_state(N, dx, a, Z, scheme, dtau, max_iter, tol,
+                                     psi.view(np.float64).ctypes.data_as(_dp), _ptr(e), ctypes.byref(it)),
+           "oracle_ground_state")
+    return psi, float(e[0]), int(it.value)
+
+
+def propagate(psi0, E, dx, dt, a, Z=1.0, scheme=FULL_CN, mask_values=None, n_begin=0, n_end=None):
+    """Propagate one instance over steps [n_begin, n_end) of the sampled field E[0..Nt].
+
+    Returns (psi, d, acc) with d, acc of length len(E): entries n_begin+1..n_end are written
+    (and n_begin when n_begin == 0); others are NaN."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    Nt = E.size - 1
+    if n_end is None:
+        n_end = Nt
+    psi = np.array(psi0, dtype=np.complex128, copy=True)
+    d = np.full(E.size, np.nan)
+    acc = np.full(E.size, np.nan)
+    m = None if mask_values is None else np.ascontiguousarray(mask_values, dtype=np.float64)
+    _check(lib().oracle_propagate(psi.size, dx, a, Z, scheme, dt, _ptr(m), _ptr(E), n_begin, n_end,
+                                  psi.view(np.float64).ctypes.data_as(_dp), _ptr(d), _ptr(acc)),
+           "oracle_propagate")
+    return psi, d, acc
+
+
+def spectrum(acc, dt):
+    """S_k = |sum_n a_n exp(-2 pi i k n / L)|^2 dt^2, L = number of samples (reading F)."""
+    acc = np.asarray(acc, dtype=np.float64)
+    return np.abs(np.fft.fft(acc)) ** 2 * dt * dt
+
+
+# ------------------------------------------------------------------ soft-core parameter (Sec. 3.1)
+
+def _numerov_solve_shifted(N, dx, V, sigma, rhs):
+    """Solve (M2^{-1}(-Delta2/2) + V - sigma) y = rhs  <=>  (-Delta2/2 + M2 V - sigma M2) y = M2 rhs."""
+    from scipy.linalg import solve_banded
+    inv = 1.0 / (dx * dx)
+    diag = inv + (10.0 / 12.0) * (V - sigma)
+    sup = -0.5 * inv + (V[1:] - sigma) / 12.0      # row j, column j+1 carries V_{j+1}
+    sub = -0.5 * inv + (V[:-1] - sigma) / 12.0     # row j+1, column j carries V_j
+    ab = np.zeros((3, N))
+    ab[0, 1:] = sup
+    ab[1, :] = diag
+    ab[2, :-1] = sub
+    m2rhs = (10.0 / 12.0) * rhs
+    m2rhs[1:] += rhs[:-1] / 12.0
+    m2rhs[:-1] += rhs[1:] / 12.0
+    return solve_banded((1, 1), ab, m2rhs)
+
+
+def lowest_eigenvalue(N, dx, a, Z=1.0, scheme=FULL_CN):
+    """Lowest eigenvalue of the scheme's discrete field-free Hamiltonian.
+
+    FULL_CN: symmetric tridiagonal eigensolver.  NUMEROV_SPLIT: shifted inverse iteration on
+    M2^{-1}(-Delta2/2) + V, started at the three-point value, with Rayleigh quotients."""
+    from scipy.linalg import eigh_tridiagonal
+    x, V, _ = grid(N, dx, a, Z)
+    inv = 1.0 / (dx * dx)
+    w = eigh_tridiagonal(inv + V, np.full(N - 1, -0.5 * inv), select="i", select_range=(0, 0),
+                         eigvals_only=True)
+    e_fd = float(w[0])
+    if scheme == FULL_CN:
+        return e_fd
+    sigma = e_fd - 1e-3
+    y = np.exp(-x * x)
+    e = e_fd
+    for _ in range(200):
+        y = _numerov_solve_shifted(N, dx, V, sigma, y)
+        y /= np.linalg.norm(y)
+        e_new = energy(y.astype(np.complex128), dx, a, Z, NUMEROV_SPLIT)
+        if abs(e_new - e) < 1e-15:
+            e = e_new
+            break
+        e = e_new
+    return e
+
+
+def fit_softening(target, N, dx, Z=1.0, scheme=FULL_CN, lo=0.2, hi=6.0):
+    """Soft-core a such that the discrete ground-state energy equals ``target``."""
+    from scipy.optimize import brentq
+    return brentq(lambda a: lowest_eigenvalue(N, dx, a, Z, scheme) - target, lo, hi, xtol=1e-14, rtol=1e-15,
+                  maxiter=200)
+
+
+# ------------------------------------------------------------------ many instances, one per process
+
+def _propagate_job(args):
+    (psi0, E, dx, dt, a, Z, scheme, mask_values) = args
+    _, d, acc = propagate(psi0, E, dx, dt, a, Z, scheme, mask_values)
+    return d, acc
+
+
+def propagate_many(jobs, workers):
+    """Run ``propagate`` for each job tuple (psi0, E, dx, dt, a, Z, scheme, mask) in a spawned pool."""
+    import multiprocessing as mp
+    build()
+    if workers <= 1 or len(jobs) <= 1:
+        return [_propagate_job(j) for j in jobs]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=workers) as pool:
+        return pool.map(_propagate_job, jobs, chunksize=1)

@@ -1,0 +1,295 @@
+"""Pins of the FP64 oracle against what the mathematics fixes (no GPU).
+
+Each test would fail on a plausible mistake in the oracle: a dropped term, a wrong sign or
+index, a transposed operand, the wrong time level of the field.  None of them re-types the
+oracle's own formulas: they compare against closed forms, brute-force eigensolvers,
+invariants, symmetry and convergence orders.
+"""
+import numpy as np
+import pytest
+from scipy.fft import dst, idst
+from scipy.linalg import eigh
+
+FULL_CN, NUMEROV = 0, 1
+
+
+def _gauss(x, x0, sigma, p0):
+    return (2 * np.pi * sigma ** 2) ** -0.25 * np.exp(-((x - x0) ** 2) / (4 * sigma ** 2) + 1j * p0 * (x - x0))
+
+
+def _norm(psi, dx):
+    return float(np.sum(np.abs(psi) ** 2) * dx)
+
+
+def _sin2_pulse(Nt, dt, E0, w, ncyc):
+    t = np.arange(Nt + 1) * dt
+    Tp = ncyc * 2 * np.pi / w
+    return np.where(t <= Tp, E0 * np.sin(np.pi * t / Tp) ** 2 * np.cos(w * (t - Tp / 2)), 0.0)
+
+
+# ---------------------------------------------------------------- free propagation: exact discrete pin
+
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_free_propagation_matches_dst_eigenbasis(oracle_mod, scheme):
+    """V = 0, E = 0, no mask.  -Delta2/2 (and M2^{-1}(-Delta2/2)) on the Dirichlet grid are diagonal in
+    the DST-I basis with eigenvalues lam_k = (2/dx^2) sin^2(k pi / (2(N+1))) (Numerov: lam_k / (1 - s_k/3),
+    s_k = sin^2(...)); Crank-Nicolson multiplies mode k by (1 - i h lam_k)/(1 + i h lam_k) per step."""
+    N, dx, dt, nsteps = 200, 0.3, 0.05, 100
+    x, _, _ = oracle_mod.grid(N, dx, 1.0, Z=0.0)
+    psi0 = _gauss(x, -5.0, 2.0, 1.5)
+    E = np.zeros(nsteps + 1)
+    psi, _, _ = oracle_mod.propagate(psi0, E, dx, dt, 1.0, Z=0.0, scheme=scheme)
+    k = np.arange(1, N + 1)
+    s = np.sin(k * np.pi / (2 * (N + 1))) ** 2
+    lam = 2.0 / dx ** 2 * s
+    if scheme == NUMEROV:
+        lam = lam / (1.0 - s / 3.0)
+    h = dt / 2
+    fac = ((1 - 1j * h * lam) / (1 + 1j * h * lam)) ** nsteps
+    coef = dst(psi0.real, type=1, norm="ortho") + 1j * dst(psi0.imag, type=1, norm="ortho")
+    coef = coef * fac
+    exact = idst(coef.real, type=1, norm="ortho") + 1j * idst(coef.imag, type=1, norm="ortho")
+    assert np.max(np.abs(psi - exact)) < 1e-12
+
+
+def test_free_gaussian_closed_form_second_order(oracle_mod):
+    """Continuous free Gaussian packet: the FULL_CN error falls ~4x when dx and dt are halved."""
+    T, x0, sigma, p0 = 4.0, -3.0, 1.5, 1.0
+    errs = []
+    for dx, dt in [(0.2, 0.1), (0.1, 0.05), (0.05, 0.025)]:
+        N = int(round(80 / dx))
+        x, _, _ = oracle_mod.grid(N, dx, 1.0, Z=0.0)
+        nsteps = int(round(T / dt))
+        psi, _, _ = oracle_mod.propagate(_gauss(x, x0, sigma, p0), np.zeros(nsteps + 1), dx, dt, 1.0, Z=0.0)
+        c = 1 + 1j * T / (2 * sigma ** 2)
+        exact = ((2 * np.pi * sigma ** 2) ** -0.25 * c ** -0.5
+                 * np.exp(-((x - x0 - p0 * T) ** 2) / (4 * sigma ** 2 * c) + 1j * p0 * (x - x0) - 1j * p0 ** 2 * T / 2))
+        errs.append(np.sqrt(np.sum(np.abs(psi - exact) ** 2) * dx))
+    assert errs[0] < 5e-2
+    assert 3.5 < errs[0] / errs[1] < 4.5
+    assert 3.5 < errs[1] / errs[2] < 4.5
+
+
+# ---------------------------------------------------------------- norm, reversibility, symmetry
+
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_norm_conserved_with_field(oracle_mod, scheme):
+    N, dx, dt = 800, 0.2, 0.05
+    a = 1.19
+    psi0, _, _ = oracle_mod.ground_state(N, dx, a, scheme=scheme, tol=1e-12)
+    E = _sin2_pulse(1500, dt, 0.05, 0.057, 1)
+    psi, d, acc = oracle_mod.propagate(psi0, E, dx, dt, a, scheme=scheme)
+    assert abs(_norm(psi, dx) - 1.0) < 1e-12
+    assert np.all(np.isfinite(d)) and np.all(np.isfinite(acc))
+
+
+def test_mask_reduces_norm_monotonically(oracle_mod):
+    N, dx, dt = 600, 0.2, 0.05
+    a = 1.19
+    psi0, _, _ = oracle_mod.ground_state(N, dx, a, tol=1e-12)
+    E = _sin2_pulse(1200, dt, 0.12, 0.057, 1)
+    m = oracle_mod.mask(N, dx, 20.0, 0.125)
+    norms = []
+    psi = psi0
+    for c in range(4):
+        psi, _, _ = oracle_mod.propagate(psi, E, dx, dt, a, mask_values=m, n_begin=c * 300, n_end=(c + 1) * 300)
+        norms.append(_norm(psi, dx))
+    assert norms[-1] < 1.0 - 1e-7
+    assert all(b <= a_ + 1e-13 for a_, b in zip([1.0] + norms[:-1], norms))
+
+
+def test_reversibility_full_cn(oracle_mod):
+    """FULL_CN is exactly reversible: stepping back with -dt and the reversed field inverts each step."""
+    N, dx, dt = 500, 0.2, 0.05
+    a = 1.19
+    psi0, _, _ = oracle_mod.ground_state(N, dx, a, tol=1e-12)
+    E = _sin2_pulse(800, dt, 0.08, 0.057, 1)
+    psi1, _, _ = oracle_mod.propagate(psi0, E, dx, dt, a)
+    psi2, _, _ = oracle_mod.propagate(psi1, E[::-1].copy(), dx, -dt, a)
+    assert np.max(np.abs(psi2 - psi0)) < 1e-12
+
+
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_field_reversal_symmetry(oracle_mod, scheme):
+    """Symmetric grid and potential: E -> -E maps x -> -x, so d -> -d and a -> -a."""
+    N, dx, dt = 500, 0.2, 0.05
+    a = 1.19
+    psi0, _, _ = oracle_mod.ground_state(N, dx, a, scheme=scheme, tol=1e-12)
+    E = _sin2_pulse(600, dt, 0.08, 0.057, 1)
+    m = oracle_mod.mask(N, dx, 20.0, 0.125)
+    _, d1, a1 = oracle_mod.propagate(psi0, E, dx, dt, a, scheme=scheme, mask_values=m)
+    _, d2, a2 = oracle_mod.propagate(psi0, -E, dx, dt, a, scheme=scheme, mask_values=m)
+    assert np.max(np.abs(d1 + d2)) < 1e-11 * np.max(np.abs(d1))
+    assert np.max(np.abs(a1 + a2)) < 1e-11 * np.max(np.abs(a1))
+
+
+# ---------------------------------------------------------------- ground state
+
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_ground_state_matches_dense_eigensolver(oracle_mod, scheme):
+    """Imaginary time vs. dense diagonalisation of the discrete H0 on a tiny grid."""
+    N, dx, a = 96, 0.25, 1.19
+    x, V, _ = oracle_mod.grid(N, dx, a)
+    lap = (np.diag(np.full(N - 1, 1.0), -1) - 2 * np.eye(N) + np.diag(np.full(N - 1, 1.0), 1)) / dx ** 2
+    if scheme == FULL_CN:
+        H = -0.5 * lap + np.diag(V)
+    else:
+        M2 = np.eye(N) + dx ** 2 / 12.0 * lap
+        H = np.linalg.solve(M2, -0.5 * lap) + np.diag(V)
+        H = 0.5 * (H + H.T)
+    w, U = eigh(H)
+    psi, e, it = oracle_mod.ground_state(N, dx, a, scheme=scheme, tol=1e-15, max_iter=20000)
+    assert abs(e - w[0]) < 1e-12
+    u = U[:, 0] / np.sqrt(dx)
+    overlap = abs(np.sum(np.conj(psi) * u) * dx)
+    assert overlap > 1 - 1e-12
+    assert abs(oracle_mod.lowest_eigenvalue(N, dx, a, scheme=scheme) - w[0]) < 1e-12
+
+
+def test_softcore_fit_and_discretisation_orders(oracle_mod):
+    """a^2 = 2 soft-core: three-point energies converge at order 2, Numerov at order 4, and both
+    Richardson limits agree with each other (two independent discretisations, same continuum value)."""
+    a = np.sqrt(2.0)
+    e_fd, e_nu = [], []
+    for dx in (0.2, 0.1, 0.05):
+        N = int(round(400 / dx))
+        e_fd.append(oracle_mod.lowest_eigenvalue(N, dx, a, scheme=FULL_CN))
+        e_nu.append(oracle_mod.lowest_eigenvalue(N, dx, a, scheme=NUMEROV))
+    r_fd = (e_fd[0] - e_fd[1]) / (e_fd[1] - e_fd[2])
+    r_nu = (e_nu[0] - e_nu[1]) / (e_nu[1] - e_nu[2])
+    assert 3.8 < r_fd < 4.2
+    assert 15.0 < r_nu < 17.0
+    lim_fd = e_fd[2] + (e_fd[2] - e_fd[1]) / 3.0
+    lim_nu = e_nu[2] + (e_nu[2] - e_nu[1]) / 15.0
+    assert abs(lim_fd - lim_nu) < 1e-8
+    assert abs(lim_nu + 0.5) < 1e-7           # the hydrogen-like soft-core model
+    # the fit helper reproduces its target on the discrete operator
+    a_fit = oracle_mod.fit_softening(-0.579, 400, 0.2)
+    assert abs(oracle_mod.lowest_eigenvalue(400, 0.2, a_fit) + 0.579) < 1e-12
+
+
+def test_stationarity_of_discrete_eigenstate(oracle_mod):
+    """Field off, mask off: an exact eigenvector of the discrete H0 only acquires the CN phase
+    ((1 - i h E)/(1 + i h E))^n; <x> and <dV/dx> vanish by parity."""
+    from scipy.linalg import eigh_tridiagonal
+    N, dx, dt, a, n = 400, 0.2, 0.05, 1.19, 300
+    x, V, _ = oracle_mod.grid(N, dx, a)
+    w, U = eigh_tridiagonal(1 / dx ** 2 + V, np.full(N - 1, -0.5 / dx ** 2), select="i", select_range=(0, 0))
+    psi0 = (U[:, 0] / np.sqrt(dx)).astype(np.complex128)
+    psi, d, acc = oracle_mod.propagate(psi0, np.zeros(n + 1), dx, dt, a)
+    h = dt / 2
+    ph = ((1 - 1j * h * w[0]) / (1 + 1j * h * w[0])) ** n
+    assert np.max(np.abs(psi - ph * psi0)) < 1e-12
+    assert np.max(np.abs(d)) < 1e-12 and np.max(np.abs(acc)) < 1e-12
+
+
+# ---------------------------------------------------------------- field coupling, observables
+
+def test_ramped_field_free_electron_midpoint_order(oracle_mod):
+    """V = 0, E(t) = alpha t:  <x>(t) = x0 + p0 t - alpha t^3 / 6 exactly in the continuum.
+    FULL_CN takes the field at the midpoint of each step; feeding it the field shifted by half a
+    step (which is what taking E_n instead of the midpoint would amount to) gives a first-order
+    error that is an order of magnitude larger and halves with dt."""
+    alpha, T, x0, sigma, p0 = 0.02, 6.0, 0.0, 2.0, 0.3
+    dx = 0.02
+    N = int(round(90 / dx))
+    x, _, _ = oracle_mod.grid(N, dx, 1.0, Z=0.0)
+    exact = x0 + p0 * T - alpha * T ** 3 / 6
+    good, shifted = [], []
+    for dt in (0.2, 0.1):
+        n = int(round(T / dt))
+        E = alpha * np.arange(n + 1) * dt
+        _, d, _ = oracle_mod.propagate(_gauss(x, x0, sigma, p0), E, dx, dt, 1.0, Z=0.0)
+        good.append(abs(d[-1] - exact))
+        _, d2, _ = oracle_mod.propagate(_gauss(x, x0, sigma, p0), E - alpha * dt / 2, dx, dt, 1.0, Z=0.0)
+        shifted.append(abs(d2[-1] - exact))
+    assert good[0] < 0.1 * shifted[0] and good[1] < 0.1 * shifted[1]
+    assert 1.8 < shifted[0] / shifted[1] < 2.2
+    assert good[0] / good[1] > 3.0
+
+
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_ehrenfest_acceleration(oracle_mod, scheme):
+    """a_n = <dV/dx> + E_n equals -d^2<x>/dt^2 (App. A, Eq. "Current_der_TDSE1D" with Ehrenfest's
+    theorem), up to the discretisation error, which shrinks when dx and dt are refined.  The window
+    ends before any part of the packet reaches the walls (no mask here)."""
+    res = []
+    for dx, dt in [(0.2, 0.05), (0.1, 0.025)]:
+        N = int(round(240 / dx))
+        a = 1.19
+        psi0, _, _ = oracle_mod.ground_state(N, dx, a, scheme=scheme, tol=1e-13)
+        n = int(round(200.0 / dt))
+        E = _sin2_pulse(n, dt, 0.06, 0.057, 2)
+        _, d, acc = oracle_mod.propagate(psi0, E, dx, dt, a, scheme=scheme)
+        dd = (d[2:] - 2 * d[1:-1] + d[:-2]) / dt ** 2
+        res.append(np.max(np.abs(dd + acc[1:-1])) / np.max(np.abs(acc)))
+    assert res[0] < 2e-2
+    assert res[0] / res[1] > 2.0
+
+
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_dipole_sign_under_static_field(oracle_mod, scheme):
+    """A weak static field E > 0 pushes the electron (charge -1) towards negative x: <x> < 0
+    while the acceleration-form source <dV/dx> + E stays consistent with it."""
+    N, dx, dt, a = 600, 0.2, 0.05, 1.19
+    psi0, _, _ = oracle_mod.ground_state(N, dx, a, scheme=scheme, tol=1e-13)
+    n = 400
+    E = 0.002 * np.minimum(1.0, np.arange(n + 1) * dt / 10.0)
+    _, d, acc = oracle_mod.propagate(psi0, E, dx, dt, a, scheme=scheme)
+    assert d[-1] < 0.0
+    assert acc[5] > 0.0
+
+
+def test_schemes_agree_to_discretisation_error(oracle_mod):
+    """FULL_CN and the paper's NUMEROV_SPLIT discretise the same equation: their dipoles agree up to
+    the discretisation errors, and the gap shrinks when dx and dt are halved."""
+    gaps = []
+    for dx, dt in [(0.2, 0.05), (0.1, 0.025)]:
+        N = int(round(200 / dx))
+        n = int(round(150.0 / dt))
+        E = _sin2_pulse(n, dt, 0.05, 0.057, 1)
+        out = []
+        for scheme in (FULL_CN, NUMEROV):
+            a = oracle_mod.fit_softening(-0.579, N, dx, scheme=scheme)
+            psi0, _, _ = oracle_mod.ground_state(N, dx, a, scheme=scheme, tol=1e-13)
+            _, d, _ = oracle_mod.propagate(psi0, E, dx, dt, a, scheme=scheme)
+            out.append(d)
+        gaps.append(np.max(np.abs(out[0] - out[1])) / np.max(np.abs(out[0])))
+    assert gaps[0] < 5e-2
+    assert gaps[0] / gaps[1] > 2.0
+
+
+# ---------------------------------------------------------------- mask and spectrum
+
+def test_mask_shape(oracle_mod):
+    N, dx, w, p = 2000, 0.2, 20.0, 0.125
+    x, _, _ = oracle_mod.grid(N, dx, 1.0)
+    m = oracle_mod.mask(N, dx, w, p)
+    xb = N * dx / 2 - w
+    assert np.all(m[np.abs(x) <= xb] == 1.0)
+    edge = np.abs(x) > xb
+    assert np.all((m[edge] < 1.0) & (m[edge] >= 0.0))
+    right = x > xb
+    assert np.all(np.diff(m[right]) <= 0.0)
+    assert np.allclose(m, m[::-1], atol=0, rtol=0)
+    j = np.argmin(np.abs(x - (xb + w / 2)))
+    assert abs(m[j] - np.cos(np.pi / 2 * (x[j] - xb) / w) ** p) < 1e-15
+    assert abs(np.interp(xb + w / 2, x, m) - 2 ** (-p / 2)) < 2e-3
+    assert np.all(oracle_mod.mask(N, dx, 0.0, p) == 1.0)
+
+
+def test_spectrum_against_direct_sum(oracle_mod):
+    rng = np.random.default_rng(5)
+    L, dt = 37, 0.3
+    a = rng.standard_normal(L)
+    S = oracle_mod.spectrum(a, dt)
+    for k in range(L):
+        s = 0j
+        for n in range(L):
+            s += a[n] * np.exp(-2j * np.pi * k * n / L)
+        assert abs(S[k] - abs(s) ** 2 * dt * dt) < 1e-12 * (1 + abs(s) ** 2)
+    k0 = 5
+    tone = np.cos(2 * np.pi * k0 * np.arange(L) / L)
+    St = oracle_mod.spectrum(tone, dt)
+    assert abs(St[k0] - (L / 2) ** 2 * dt * dt) < 1e-10
+    assert np.max(np.delete(St, [k0, L - k0])) < 1e-20
