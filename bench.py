@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Benchmark of the batched 1D-TDSE hot path on GB300.
+
+Workload (default): the macroscopic volume batch -- 64 radial x 128 axial = 8192 independent
+length-gauge TDSE instances, N = 4096 (dx = 0.15), dt = 0.02, 800 nm 10-cycle sin^2 pulse
+(Nt = 55159 steps), synthetic Gaussian-beam fields, FP64, FULL_CN, cos^(1/8) mask.
+
+One benchmark step = one tdse_propagate call that advances every instance by one chunk of
+ceil(Nt / (warmup + steps)) time steps (RHS, tridiagonal solve, mask and d/a observables of every
+grid point of every instance, every time step).  Warm-up plus timed steps together cover the
+whole propagation exactly once, so the run also yields complete a(t) for the spectrum and the
+oracle comparison.  The soft-core fit and ground state (once per grid class) and the spectrum
+(once per job) are timed separately and reported beside the step throughput.
+
+Metric: grid-point-steps/s = instances x N x time steps / seconds (whole job over all GPUs).
+
+--impl reference runs the FP64 CPU oracle (the reference arm of this build) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1D-TDSE grid-point-steps/s (batched) & % pipe roofline; mixed vs FP64 at stated error"
+UNIT = "grid-point-steps/s"
+FLOPS_PER_POINT_STEP = 48.0          # algorithmic FULL_CN work per grid-point step (FMA = 2 flops)
+FP64_FMA_PER_CLK_PER_SM = 2.0        # GB300 FP64 pipe: 2 FMA/clk/SM (1.2 TFLOP/s measured at 2.0 GHz)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_propagate_fp64_volume_traffic.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2507_04115_gb300", "csrc", "tdse_kernels.cu")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["own", "reference"], default="own")
+    p.add_argument("--e2e-steps", type=int, default=2, help="chunks timed end to end through host buffers")
+    p.add_argument("--cpu-baseline", type=int, default=1, help="time the oracle on the host cores (rank 0, N = 1)")
+    p.add_argument("--cpu-instances", type=int, default=0, help="oracle sample size (0 = one per core, max 16)")
+    p.add_argument("--ref-steps-per-step", type=int, default=8192, help="oracle time steps per reference step")
+    p.add_argument("--segments", type=int, default=0, help="override the planner's segments per instance")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------- helpers
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_traffic_per_point_step():
+    """DRAM bytes per grid-point step of k_propagate_fp64 from the committed ncu summary, or None
+    when the summary is missing or the kernel source changed since the capture."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    if kv.get("source_sha256") != sha:
+        return None
+    try:
+        return float(kv["bytes_per_point_step"])
+    except (KeyError, ValueError):
+        return None
+
+
+def harmonic_cutoff(E0, omega, ip=0.579):
+    up = E0 ** 2 / (4 * omega ** 2)
+    return (ip + 3.17 * up) / omega
+
+
+def spectral_errors(S, S_ref, omega0, dt, L, q_cut):
+    """(i) relative L2 of S over bins with q <= 1.5 q_cut; (ii) max over odd harmonics q <= q_cut of
+    |S_q - S_q^ref| / S_q^ref with S_q the power integrated over +-omega0/2 around q omega0."""
+    k = np.arange(S.size)
+    q = k * 2 * np.pi / (L * dt) / omega0
+    sel = q <= 1.5 * q_cut
+    l2 = float(np.linalg.norm(S[sel] - S_ref[sel]) / np.linalg.norm(S_ref[sel]))
+    worst = 0.0
+    for h in range(1, int(q_cut) + 1, 2):
+        win = (q > h - 0.5) & (q <= h + 0.5)
+        if win.any():
+            a, b = S[win].sum(), S_ref[win].sum()
+            worst = max(worst, abs(a - b) / b)
+    return l2, worst
+
+
+def _oracle_job(args):
+    import oracle
+    (psi0, E, dx, dt, a, mask, n_end) = args
+    _, d, acc = oracle.propagate(psi0, E, dx, dt, a, mask_values=mask, n_begin=0, n_end=n_end)
+    return acc
+
+
+def run_oracle_pool(jobs, workers):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(processes=workers)
+    return pool
+
+
+# ------------------------------------------------------------------------------------------- own arm
+
+def own_arm(args):
+    import torch
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+
+    from paper_2507_04115_gb300 import build, inputs, softcore, tdse
+    build.build()
+    tdse.load()
+    import oracle  # test infrastructure: used only for the CPU baseline and the spectral check
+    oracle.build()
+
+    # weak scaling: rank r owns its own 64 x 128 slice of a (64 x 128 world)-point volume
+    full = inputs.gaussian_beam_volume(n_z=128 * world) if world > 1 else inputs.volume_batch()
+    n = 8192
+    sl = slice(rank * n, (rank + 1) * n)
+    N, dx, dt = int(full.N[0]), float(full.dx[0]), full.dt
+    Nt = int(full.n_steps[0])
+    omega, ncyc = float(full.omega[0]), float(full.n_cycles[0])
+    E0, phi = full.E0[sl], full.phi[sl]
+    n_chunks = args.warmup + args.steps
+    S = int(math.ceil(Nt / n_chunks))
+    chunks = [(c * S, min(Nt, (c + 1) * S)) for c in range(n_chunks)]
+
+    # CPU baseline: oracle instances started now in spawned workers, running while the GPU works
+    cpu_pool = cpu_async = None
+    cores = 0
+    sample_idx = []
+    t_cpu0 = None
+    if args.cpu_baseline and rank == 0 and world == 1:
+        cores = args.cpu_instances or min(16, os.cpu_count() or 1)
+        sample_idx = list(inputs.subsample(n, cores, 101))
+
+    t0 = time.time()
+    a_soft = softcore.fit_softening(full.target_energy, N, dx, device=local_rank)
+    t_fit = time.time() - t0
+
+    if sample_idx:
+        psi0_o, _, _ = oracle.ground_state(N, dx, a_soft)
+        m = oracle.mask(N, dx, full.mask_width, full.mask_exponent)
+        jobs = [(psi0_o, inputs.sin2_pulse(Nt, dt, E0[i], omega, ncyc, phi[i]), dx, dt, a_soft, m, Nt)
+                for i in sample_idx]
+        cpu_pool = run_oracle_pool(jobs, cores)
+        t_cpu0 = time.time()
+        cpu_async = cpu_pool.map_async(_oracle_job, jobs, chunksize=1)
+
+    offs = np.arange(n + 1, dtype=np.int64) * (S + 1)
+    batch = tdse.Batch([N] * n, dx, a_soft, [Nt] * n, dt, row_offsets=offs,
+                       absorber=(full.mask_width, full.mask_exponent), device=local_rank)
+    if args.segments:
+        batch.set_segments(args.segments)
+    plan = batch.plan()
+    stream = torch.cuda.current_stream(dev)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    batch.ground_state()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_gs_ms = ev0.elapsed_time(ev1)
+
+    # device-resident chunk inputs and outputs
+    Ec = []
+    for (s0, s1) in chunks:
+        e = torch.zeros((n, S + 1), dtype=torch.float64, device=dev)
+        full_rows = torch.empty((n, s1 - s0 + 1), dtype=torch.float64, device=dev)
+        tt = (torch.arange(s0, s1 + 1, dtype=torch.float64, device=dev) * dt)
+        Tp = ncyc * 2 * math.pi / omega
+        env = torch.where(tt <= Tp, torch.sin(math.pi * tt / Tp) ** 2, torch.zeros_like(tt))
+        e0 = torch.as_tensor(E0, device=dev)
+        ph = torch.as_tensor(phi, device=dev)
+        full_rows.copy_(e0[:, None] * env[None, :] * torch.cos(omega * (tt[None, :] - 0.5 * Tp) + ph[:, None]))
+        e[:, : s1 - s0 + 1] = full_rows
+        Ec.append(e.reshape(-1))
+    dc = [torch.zeros(n * (S + 1), dtype=torch.float64, device=dev) for _ in chunks]
+    ac = [torch.zeros(n * (S + 1), dtype=torch.float64, device=dev) for _ in chunks]
+
+    for c in range(args.warmup):
+        s0, s1 = chunks[c]
+        batch.propagate(Ec[c], dc[c], ac[c], s0, s1, sample_base=s0, stream=stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        c = args.warmup + k
+        s0, s1 = chunks[c]
+        starts[k].record(stream)
+        batch.propagate(Ec[c], dc[c], ac[c], s0, s1, sample_base=s0, stream=stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launch_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.steps)]
+    total_ms = starts[0].elapsed_time(ends[-1])
+    timed_steps = sum(chunks[args.warmup + k][1] - chunks[args.warmup + k][0] for k in range(args.steps))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pt_steps = float(n) * N * timed_steps * world
+    value = pt_steps / (total_ms * 1e-3)
+    bad = batch.check(stream)
+
+    # a(t) of the whole propagation and its spectrum (once per job)
+    acc_full = torch.empty((n, Nt + 1), dtype=torch.float64, device=dev)
+    for c, (s0, s1) in enumerate(chunks):
+        blk = ac[c].view(n, S + 1)
+        lo = 0 if c == 0 else 1
+        acc_full[:, s0 + lo: s1 + 1] = blk[:, lo: s1 - s0 + 1]
+    q_cut = harmonic_cutoff(float(np.max(E0)), omega)
+    L = Nt + 1
+    k_max = min(L, int(math.ceil(1.5 * q_cut * omega * L * dt / (2 * math.pi))) + 2)
+    ev0.record(stream)
+    S_dev = tdse.spectrum(acc_full.reshape(-1), np.arange(n + 1) * L, dt, 0, k_max, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_spec_ms = ev0.elapsed_time(ev1)
+
+    # end to end: host (pinned) field chunks in, d and a chunks out, through the public binding
+    e2e = None
+    if args.e2e_steps > 0:
+        batch.ground_state()
+        n_e2e = min(args.e2e_steps, n_chunks)
+        Eh = [Ec[c].cpu().pin_memory() for c in range(n_e2e)]
+        dh = [torch.empty(n * (S + 1), dtype=torch.float64).pin_memory() for _ in range(n_e2e)]
+        ah = [torch.empty(n * (S + 1), dtype=torch.float64).pin_memory() for _ in range(n_e2e)]
+        # one untimed pass warms torch's caching allocator for the binding's device copies
+        batch.propagate(Eh[0], dh[0], ah[0], chunks[0][0], chunks[0][1], sample_base=chunks[0][0], stream=stream)
+        batch.ground_state()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        e0_ = torch.cuda.Event(enable_timing=True)
+        e1_ = torch.cuda.Event(enable_timing=True)
+        e0_.record(stream)
+        for c in range(n_e2e):
+            s0, s1 = chunks[c]
+            batch.propagate(Eh[c], dh[c], ah[c], s0, s1, sample_base=s0, stream=stream)
+        e1_.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0_.elapsed_time(e1_)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e_pts = float(n) * N * sum(chunks[c][1] - chunks[c][0] for c in range(n_e2e)) * world
+        e2e = {"value": e2e_pts / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(n * (S + 1) * 8), "d2h_bytes_per_step": int(2 * n * (S + 1) * 8),
+               "steps": n_e2e, "how": "Batch.propagate with pinned CPU tensors: H2D field chunk, kernel, "
+                                     "D2H d and a chunks, CUDA events on the launching stream"}
+
+    # CPU baseline results and spectral error of the sampled instances
+    cpu_baseline = None
+    spec_err = None
+    if cpu_async is not None:
+        accs = cpu_async.get()
+        t_cpu = time.time() - t_cpu0
+        cpu_pool.close()
+        cpu_pool.join()
+        cpu_pts = float(len(sample_idx)) * N * Nt
+        cpu_baseline = {"value": cpu_pts / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": "%d instances of this workload (seeded subsample), full %d-step propagation each, "
+                                  "one spawned process per core, while the GPU ran" % (len(sample_idx), Nt)}
+        S_host = S_dev.cpu().numpy()
+        acc_host = acc_full.cpu().numpy()
+        l2s, worst = [], []
+        series = 0.0
+        for j, i in enumerate(sample_idx):
+            S_ref = oracle.spectrum(accs[j], dt)[:k_max]
+            l2, w = spectral_errors(S_host[i], S_ref, omega, dt, L, q_cut)
+            l2s.append(l2)
+            worst.append(w)
+            series = max(series, float(np.max(np.abs(acc_host[i] - accs[j])) / np.max(np.abs(accs[j]))))
+        spec_err = {"instances": len(sample_idx), "rel_l2_max": max(l2s), "harmonic_rel_max": max(worst),
+                    "a_series_rel_max": series, "q_cut": q_cut, "bound": 1e-6}
+
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    pts_per_launch = float(n) * N * (timed_steps / args.steps)
+    achieved = FLOPS_PER_POINT_STEP * pts_per_launch / avg_launch_s
+    peak = FP64_FMA_PER_CLK_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6
+    tpp = kernel_traffic_per_point_step()
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": (tpp * pts_per_launch) if tpp is not None else None,
+                "kernel": "k_propagate_fp64", "pipe": "fp64",
+                "peak_how": "2 FP64 FMA/clk/SM x 152 SMs x 2 flops x 2070 MHz (unit counts at max clock)",
+                "achieved_how": "48 flops per grid-point step x points x steps per launch / mean CUDA-event "
+                                "launch time"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "volume batch 64r x 128z = 8192 instances per GPU, N=4096 dx=0.15, dt=0.02, "
+                                  "800 nm 10-cycle sin^2 Gaussian-beam fields, FP64 FULL_CN, cos^(1/8) mask",
+                      "instances_per_gpu": n, "N": N, "dx": dx, "dt": dt, "Nt": Nt, "chunk_steps": S,
+                      "step": "one tdse_propagate call advancing every instance by chunk_steps time steps",
+                      "l2": "inputs larger than L2: psi %.0f MB + scratch %.0f MB per GPU" %
+                            (plan["psi_bytes"] / 1e6, plan["scratch_bytes"] / 1e6),
+                      "precision": "fp64", "scheme": "full_cn", "segments": plan["segments"],
+                      "halo": plan["halo"], "parallelism": "instances sharded over GPUs, no collective"},
+           "solves_per_s": value / (N * Nt),
+           "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clk,
+           "gpu_launches": args.steps, "nonfinite_instance": bad,
+           "setup": {"softening_fit_s": t_fit, "softening": a_soft, "ground_state_ms": t_gs_ms,
+                     "spectrum_ms": t_spec_ms, "spectrum_bins": k_max},
+           "spectral_error": spec_err}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    batch.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------- reference arm
+
+def reference_arm(args):
+    """The FP64 CPU oracle on the host cores: each step propagates a bounded sample of the same
+    workload (one instance per core, ref-steps-per-step time steps each)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    import oracle
+    from paper_2507_04115_gb300 import inputs
+    oracle.build()
+    wl = inputs.volume_batch()
+    N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+    Nt = int(wl.n_steps[0])
+    cores = args.cpu_instances or min(16, os.cpu_count() or 1)
+    T = min(Nt, args.ref_steps_per_step)
+    a = oracle.fit_softening(wl.target_energy, N, dx)
+    psi0, _, _ = oracle.ground_state(N, dx, a)
+    m = oracle.mask(N, dx, wl.mask_width, wl.mask_exponent)
+    idx = inputs.subsample(wl.n_inst, cores, 101)
+    jobs = [(psi0, inputs.sin2_pulse(T, dt, wl.E0[i], float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi[i]), dx, dt,
+             a, m, T) for i in idx]
+    ctx = mp.get_context("spawn")
+    times = []
+    with ctx.Pool(processes=cores) as pool:
+        for k in range(args.warmup + args.steps):
+            t0 = time.time()
+            pool.map(_oracle_job, jobs, chunksize=1)
+            if k >= args.warmup:
+                times.append(time.time() - t0)
+    pts = float(len(jobs)) * N * T
+    total = sum(times)
+    value = pts * len(times) / total
+    sample = ("%d instances x %d steps of the volume batch per step (seeded subsample), one spawned process per "
+              "core" % (len(jobs), T))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "volume batch 64r x 128z = 8192 instances, N=4096 dx=0.15, dt=0.02, 800 nm "
+                                  "10-cycle sin^2 Gaussian-beam fields, FP64 FULL_CN, cos^(1/8) mask",
+                      "N": N, "dx": dx, "dt": dt, "Nt": Nt, "sample": sample},
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value, "unit": UNIT},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        own_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * tdse.h -- C ABI of libtdse.so, a GB300 (sm_103a) engine for batches of independent
+ * one-dimensional time-dependent Schroedinger equations in the length gauge
+ * (arXiv:2507.04115, Sec. 3.1 Eqs. "Hamiltonian (a)" and "SC potential"; Sec. 4.2):
+ *
+ *     i d/dt psi(x,t) = [ -1/2 d^2/dx^2 - Z / sqrt(x^2 + a^2) + x E(t) ] psi(x,t)
+ *
+ * one per macroscopic point, each driven by its own sampled field E(t), each emitting the
+ * position expectation d(t) = <x> and the dipole acceleration a(t) = <dV/dx + E(t)>
+ * (Sec. 3.1 Eq. "dipole acceleration"; App. A Eq. "Current_der_TDSE1D").
+ *
+ * Discretisation shared by every entry point
+ *   grid      x_j = (j - (N-1)/2) dx, j = 0..N-1, Dirichlet walls psi_{-1} = psi_N = 0
+ *             (Sec. 4.2 uses a symmetric grid; the cell-centred variant keeps N even)
+ *   time      t_n = n dt, n = 0..Nt; E_n = E(t_n); the field's time origin is t = 0 (Sec. 4.2)
+ *   schemes   TDSE_FULL_CN: Crank-Nicolson with the field in the diagonal at the midpoint
+ *                 (1 + i dt/2 H(Ebar)) psi~ = (1 - i dt/2 H(Ebar)) psi^n, Ebar = (E_n + E_{n+1})/2,
+ *                 H = -Delta2/2 + V + x Ebar, Delta2 = tridiag(1,-2,1)/dx^2
+ *             TDSE_NUMEROV_SPLIT: the paper's three substeps (Sec. 4.2, Eqs. "CN - step 4",
+ *                 "CN - step 2", "CN - step 3"): Numerov-corrected field-free CN, then the phase
+ *                 exp(-i dt E_n x_j)
+ *   absorber  after every step psi_j *= m_j, m_j = cos(pi/2 (|x_j| - x_b)/w)^p for |x_j| > x_b,
+ *             x_b = N dx/2 - w (the paper has none, Sec. 4.2; width <= 0 disables it)
+ *   output    d_n = dx sum_j x_j |psi_j|^2,  a_n = dx sum_j (dV/dx(x_j) + E_n) |psi_j|^2
+ *             for n = 0..Nt (n = 0 is the initial state); rectangle rule, sum |psi|^2 dx = 1
+ *
+ * Conventions
+ *   - "_dev" pointers are CUDA device memory owned by the caller; "_host" pointers are host
+ *     memory owned by the caller.  The batch owns its wavefunctions, tables and scratch.
+ *   - Compute entry points are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) and return a status, never abort.  The library
+ *     sets the batch's device before it launches.
+ *   - Errors: every entry point validates its arguments on the host and returns
+ *     TDSE_ERR_ARG without launching anything; a failed CUDA call returns TDSE_ERR_CUDA.
+ *     tdse_last_error() gives a message for the calling thread's last failure.
+ *   - A batch handle is not thread-safe.  Separate handles are independent.
+ *   - All floating-point values cross the boundary as IEEE double, whatever the precision.
+ */
+#ifndef TDSE_H
+#define TDSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TDSE_OK = 0,
+    TDSE_ERR_ARG = 1,        /* invalid argument; nothing was launched */
+    TDSE_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    TDSE_ERR_NONFINITE = 3,  /* an instance's norm became non-finite or grew above 1 + 1e-6 */
+    TDSE_ERR_TIMEOUT = 4,    /* reserved: a bounded device wait gave up */
+    TDSE_ERR_NOMEM = 5,      /* device or host allocation failed */
+    TDSE_ERR_STATE = 6       /* call out of order (e.g. propagate before any initial state) */
+} tdse_status;
+
+typedef enum {
+    TDSE_FP64 = 0,   /* all arithmetic and storage in IEEE double */
+    TDSE_MIXED = 1   /* psi and potential/field arithmetic in float; elimination coefficients and
+                        observable accumulation in double (reserved in this version) */
+} tdse_precision;
+
+typedef enum {
+    TDSE_FULL_CN = 0,
+    TDSE_NUMEROV_SPLIT = 1
+} tdse_scheme;
+
+/* One TDSE instance: grid size and spacing, soft-core parameter a and charge Z. */
+typedef struct {
+    int32_t N;          /* grid points, 16 <= N <= 1 << 20 */
+    double dx;          /* grid spacing (a.u.), > 0 */
+    double softening;   /* a (a.u.), > 0 */
+    double charge;      /* Z; 1 for the paper's model, 0 gives a free electron */
+} tdse_instance;
+
+/* Edge absorber: width w (a.u.) and exponent p; width <= 0 disables the mask. */
+typedef struct {
+    double width;
+    double exponent;
+} tdse_absorber;
+
+typedef struct tdse_batch tdse_batch;
+
+/* Create a batch of n_inst independent instances sharing the time step dt.
+ *   inst_host[n_inst]          per-instance grid, soft-core a and charge
+ *   n_steps_host[n_inst]       Nt_i, the number of time steps of instance i (>= 0)
+ *   row_offsets_host[n_inst+1] layout of every per-sample array (field E, outputs d and a):
+ *                              instance i owns elements [row_offsets[i], row_offsets[i+1]) of
+ *                              each; element k of the row holds sample n = sample_base + k, with
+ *                              sample_base given per call.  Non-decreasing, row_offsets[0] >= 0.
+ *   absorber                   NULL or the edge mask parameters
+ *   device                     CUDA device ordinal the batch lives on
+ * Allocates the wavefunctions (uninitialised until tdse_ground_state or tdse_set_psi), the
+ * per-instance tables and the propagation scratch on that device.  On success *out receives
+ * the handle; on failure *out is NULL and nothing stays allocated. */
+tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, double dt,
+                              const int64_t* n_steps_host, const int64_t* row_offsets_host,
+                              const tdse_absorber* absorber, tdse_precision precision,
+                              tdse_scheme scheme, int device, tdse_batch** out);
+
+/* Release everything the batch owns.  Synchronises the batch's device first.  NULL is a no-op. */
+void tdse_batch_destroy(tdse_batch* batch);
+
+/* Ground state of the field-free Hamiltonian H0 of every instance (the paper leaves the method
+ * open, Sec. 3.1 defines E_g only): imaginary-time Crank-Nicolson with the scheme's H0,
+ *     (M + dtau/2 K) psi' = (M - dtau/2 K) psi,  psi' <- psi'/sqrt(sum |psi'|^2 dx),
+ * started from exp(-x^2), stopped when |E_k - E_{k-1}| < tol or after max_iter iterations,
+ * sign fixed so that psi is positive at the grid centre.  It runs once per distinct
+ * (N, dx, a, Z) and the result is copied into every instance of that class, which also
+ * resets each instance's time to n = 0.
+ *   energies_host[n_inst]  NULL or receives E_g per instance (the call then synchronises)
+ *   iters_host[n_inst]     NULL or receives the iteration count per instance (synchronises) */
+tdse_status tdse_ground_state(tdse_batch* batch, double dtau, int64_t max_iter, double tol,
+                              double* energies_host, int64_t* iters_host, void* stream);
+
+/* Advance every instance i over the steps n = step_begin .. min(step_end, Nt_i) - 1.
+ *   E_dev   field samples: E_n of instance i at E_dev[row_offsets[i] + n - sample_base]; the call
+ *           reads n = step_begin .. min(step_end, Nt_i)
+ *   d_dev, a_dev  outputs in the same layout: d_{n+1}, a_{n+1} for every step taken, and d_n, a_n
+ *           for n = step_begin when step_begin == 0 (the initial state)
+ *   sample_base <= step_begin; every row must hold the samples the call touches.
+ * Instances with Nt_i <= step_begin are left untouched.  Chunked calls with consecutive ranges
+ * continue the same propagation. */
+tdse_status tdse_propagate(tdse_batch* batch, const double* E_dev, double* d_dev, double* a_dev,
+                           int64_t sample_base, int64_t step_begin, int64_t step_end, void* stream);
+
+/* Copy the wavefunction of instance `inst` out of / into the batch: 2N doubles, interleaved
+ * (re, im), device memory of the caller (the paper exposes psi for user post-processing,
+ * Sec. 4.2).  tdse_set_psi also marks the batch as initialised (resume from a checkpoint). */
+tdse_status tdse_get_psi(tdse_batch* batch, int64_t inst, double* psi_dev, void* stream);
+tdse_status tdse_set_psi(tdse_batch* batch, int64_t inst, const double* psi_dev, void* stream);
+
+/* Synchronise the stream and report TDSE_ERR_NONFINITE if any instance's norm became non-finite
+ * or exceeded 1 + 1e-6 during a propagation since the batch was created or last checked;
+ * *first_bad_host (may be NULL) receives the first such instance or -1.  Clears the flags. */
+tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream);
+
+/* Power spectrum of sampled signals (Sec. 3.1 / App. A: the source term enters Maxwell's
+ * equations through its Fourier transform):
+ *     S_i[k] = dt^2 |sum_{n=0}^{L_i - 1} a_i[n] exp(-2 pi i k n / L_i)|^2,  k = k_begin .. k_end - 1,
+ * a plain DFT over the L_i = row length samples of row i (no window, no padding).
+ *   a_dev     rows: row i is a_dev[offsets[i] .. offsets[i+1])   (offsets_host: host, n_rows+1)
+ *   S_dev     [n_rows][k_end - k_begin] row-major
+ * Requires 0 <= k_begin < k_end. */
+tdse_status tdse_spectrum(const double* a_dev, const int64_t* offsets_host, int64_t n_rows, double dt,
+                          int64_t k_begin, int64_t k_end, double* S_dev, void* stream);
+
+/* Plan chosen for the batch (for benchmarks and tests): number of 32-instance groups, warps per
+ * instance (segments), halo length in points, scratch bytes, and wavefunction bytes. */
+typedef struct {
+    int64_t n_groups;
+    int32_t segments;
+    int32_t halo;
+    int64_t scratch_bytes;
+    int64_t psi_bytes;
+} tdse_plan_info;
+
+tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);
+
+/* Override the number of segments (warps) per instance for later calls; 0 restores the
+ * default.  The value is clamped to what the grid and the halo allow; the scratch is resized. */
+tdse_status tdse_set_segments(tdse_batch* batch, int32_t segments);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* tdse_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDSE_H */

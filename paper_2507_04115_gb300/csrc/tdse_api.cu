@@ -1,0 +1,548 @@
+// C ABI of libtdse.so (declared in include/tdse.h): argument validation, instance grouping,
+// planning, memory ownership and kernel launches.  Host logic only; kernels live in
+// tdse_kernels.cu.
+#include "tdse.h"
+#include "tdse_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using namespace tdse;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tdse_status fail(tdse_status st, const std::string& msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+tdse_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(TDSE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TDSE_CUDA(call, what)                          \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+}  // namespace
+
+struct tdse_batch {
+    int device = 0;
+    int64_t n_inst = 0;
+    double dt = 0.0;
+    tdse_precision precision = TDSE_FP64;
+    tdse_scheme scheme = TDSE_FULL_CN;
+    int mask_on = 0;
+    double mask_width = 0.0, mask_exp = 0.0;
+    std::vector<tdse_instance> inst;
+    std::vector<int64_t> n_steps, row_off;
+    // classes and slots
+    std::vector<ClassDesc> classes;
+    std::vector<int> inst_class;
+    std::vector<int64_t> slot_of_inst;
+    std::vector<GroupDesc> groups;
+    std::vector<int> class_P, class_K;
+    std::vector<int64_t> class_group_begin, class_group_end;
+    int64_t n_slots = 0;
+    int segments_override = 0;
+    bool initialized = false;
+    // device memory
+    ClassDesc* d_cls = nullptr;
+    GroupDesc* d_groups = nullptr;
+    double* d_tab = nullptr;
+    int64_t* d_slot_row = nullptr;
+    int64_t* d_slot_nt = nullptr;
+    int64_t* d_slot_valid = nullptr;
+    double2* d_psi = nullptr;
+    double2* d_scratch = nullptr;
+    int* d_status = nullptr;
+    double* d_gs_work = nullptr;
+    int64_t* d_gs_off = nullptr;
+    double* d_gs_energy = nullptr;
+    int64_t* d_gs_iters = nullptr;
+    int64_t psi_elems = 0, scratch_elems = 0;
+};
+
+namespace {
+
+void free_device(tdse_batch* b)
+{
+    cudaFree(b->d_cls);
+    cudaFree(b->d_groups);
+    cudaFree(b->d_tab);
+    cudaFree(b->d_slot_row);
+    cudaFree(b->d_slot_nt);
+    cudaFree(b->d_slot_valid);
+    cudaFree(b->d_psi);
+    cudaFree(b->d_scratch);
+    cudaFree(b->d_status);
+    cudaFree(b->d_gs_work);
+    cudaFree(b->d_gs_off);
+    cudaFree(b->d_gs_energy);
+    cudaFree(b->d_gs_iters);
+    b->d_cls = nullptr;
+    b->d_groups = nullptr;
+    b->d_tab = nullptr;
+    b->d_slot_row = b->d_slot_nt = b->d_slot_valid = nullptr;
+    b->d_psi = b->d_scratch = nullptr;
+    b->d_status = nullptr;
+    b->d_gs_work = nullptr;
+    b->d_gs_off = nullptr;
+    b->d_gs_energy = nullptr;
+    b->d_gs_iters = nullptr;
+}
+
+// Halo length K such that beta^K < 1e-18 (the truncated sweeps then agree with the exact Thomas
+// solve below double rounding); 0 when beta is too close to 1 for truncation to pay off.
+int halo_for_beta(double beta)
+{
+    const double b = std::fabs(beta);
+    if (b >= 0.85) return 0;
+    if (b < 1e-3) return 8;
+    int K = (int)std::ceil(std::log(1e-18) / std::log(b));
+    return std::max(K, 8);
+}
+
+// Segments per instance: enough warps to fill the GPU (about 8 per SM on 152 SMs) while keeping
+// every segment at least 4 halos long.
+int plan_segments(int N, int K, int64_t total_groups, int override_P)
+{
+    if (K == 0) return 1;
+    int max_P = std::max(1, std::min(kMaxSegments, N / std::max(4 * K, 16)));
+    int P;
+    if (override_P > 0) {
+        P = override_P;
+    } else {
+        const int64_t want_warps = 152 * 8;
+        P = (int)std::min<int64_t>(kMaxSegments, (want_warps + total_groups - 1) / std::max<int64_t>(total_groups, 1));
+    }
+    return std::max(1, std::min(P, max_P));
+}
+
+// (Re)compute the per-class plan, group descriptors and scratch size, and (re)allocate scratch.
+tdse_status build_plan(tdse_batch* b)
+{
+    const int n_cls = (int)b->classes.size();
+    b->class_P.assign(n_cls, 1);
+    b->class_K.assign(n_cls, 0);
+    const int64_t total_groups = (int64_t)b->groups.size();
+    for (int c = 0; c < n_cls; ++c) {
+        const ClassDesc& C = b->classes[c];
+        int K = halo_for_beta(C.beta);
+        int P = plan_segments(C.N, K, total_groups, b->segments_override);
+        if (P == 1) K = 0;
+        b->class_P[c] = P;
+        b->class_K[c] = K;
+    }
+    int64_t sc = 0;
+    for (auto& G : b->groups) {
+        const int P = b->class_P[G.cls], K = b->class_K[G.cls];
+        G.P = P;
+        G.K = K;
+        G.m = (G.N + P - 1) / P;
+        G.rows = std::min(G.N, G.m + 2 * K);
+        G.scratch_off = sc;
+        sc += (int64_t)P * G.rows * 2 * kLanes;
+    }
+    cudaFree(b->d_scratch);
+    b->d_scratch = nullptr;
+    TDSE_CUDA(dev_alloc(&b->d_scratch, (size_t)sc), "cudaMalloc(scratch)");
+    b->scratch_elems = sc;
+    TDSE_CUDA(cudaMemcpy(b->d_groups, b->groups.data(), sizeof(GroupDesc) * b->groups.size(), cudaMemcpyHostToDevice),
+              "cudaMemcpy(groups)");
+    return TDSE_OK;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+extern "C" {
+
+const char* tdse_last_error(void) { return g_last_error.c_str(); }
+
+tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, double dt, const int64_t* n_steps_host,
+                              const int64_t* row_offsets_host, const tdse_absorber* absorber,
+                              tdse_precision precision, tdse_scheme scheme, int device, tdse_batch** out)
+{
+    if (!out) return fail(TDSE_ERR_ARG, "tdse_batch_create: out is NULL");
+    *out = nullptr;
+    if (!inst_host || !n_steps_host || !row_offsets_host) return fail(TDSE_ERR_ARG, "tdse_batch_create: NULL array");
+    if (n_inst < 1 || n_inst > (int64_t(1) << 31)) return fail(TDSE_ERR_ARG, "tdse_batch_create: n_inst out of range");
+    if (!is_finite(dt) || dt == 0.0) return fail(TDSE_ERR_ARG, "tdse_batch_create: dt must be finite and non-zero");
+    if (precision != TDSE_FP64) return fail(TDSE_ERR_ARG, "tdse_batch_create: only TDSE_FP64 is available in this build");
+    if (scheme != TDSE_FULL_CN) return fail(TDSE_ERR_ARG, "tdse_batch_create: only TDSE_FULL_CN is available in this build");
+    if (absorber && (!is_finite(absorber->width) || !is_finite(absorber->exponent) || absorber->exponent < 0.0))
+        return fail(TDSE_ERR_ARG, "tdse_batch_create: bad absorber");
+    if (row_offsets_host[0] < 0) return fail(TDSE_ERR_ARG, "tdse_batch_create: row_offsets[0] < 0");
+    for (int64_t i = 0; i < n_inst; ++i) {
+        const tdse_instance& I = inst_host[i];
+        if (I.N < 16 || I.N > (1 << 20)) return fail(TDSE_ERR_ARG, "tdse_batch_create: N out of [16, 2^20] at instance " + std::to_string(i));
+        if (!is_finite(I.dx) || I.dx <= 0.0) return fail(TDSE_ERR_ARG, "tdse_batch_create: dx <= 0 at instance " + std::to_string(i));
+        if (!is_finite(I.softening) || I.softening <= 0.0) return fail(TDSE_ERR_ARG, "tdse_batch_create: softening <= 0 at instance " + std::to_string(i));
+        if (!is_finite(I.charge)) return fail(TDSE_ERR_ARG, "tdse_batch_create: non-finite charge");
+        if (n_steps_host[i] < 0) return fail(TDSE_ERR_ARG, "tdse_batch_create: negative n_steps");
+        if (row_offsets_host[i + 1] < row_offsets_host[i]) return fail(TDSE_ERR_ARG, "tdse_batch_create: row_offsets decreasing");
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(TDSE_ERR_ARG, "tdse_batch_create: no such CUDA device");
+    DeviceGuard guard(device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "tdse_batch_create: cudaSetDevice failed");
+
+    tdse_batch* b = new tdse_batch();
+    b->device = device;
+    b->n_inst = n_inst;
+    b->dt = dt;
+    b->precision = precision;
+    b->scheme = scheme;
+    b->mask_on = absorber && absorber->width > 0.0;
+    b->mask_width = absorber ? absorber->width : 0.0;
+    b->mask_exp = absorber ? absorber->exponent : 0.0;
+    b->inst.assign(inst_host, inst_host + n_inst);
+    b->n_steps.assign(n_steps_host, n_steps_host + n_inst);
+    b->row_off.assign(row_offsets_host, row_offsets_host + n_inst + 1);
+
+    // classes: distinct (N, dx, a, Z), compared bit for bit
+    std::map<std::tuple<int32_t, uint64_t, uint64_t, uint64_t>, int> cmap;
+    b->inst_class.resize(n_inst);
+    for (int64_t i = 0; i < n_inst; ++i) {
+        const tdse_instance& I = inst_host[i];
+        uint64_t kdx, ka, kz;
+        std::memcpy(&kdx, &I.dx, 8);
+        std::memcpy(&ka, &I.softening, 8);
+        std::memcpy(&kz, &I.charge, 8);
+        auto key = std::make_tuple(I.N, kdx, ka, kz);
+        auto it = cmap.find(key);
+        int c;
+        if (it == cmap.end()) {
+            c = (int)b->classes.size();
+            cmap.emplace(key, c);
+            ClassDesc C{};
+            C.N = I.N;
+            C.dx = I.dx;
+            C.a = I.softening;
+            C.Z = I.charge;
+            C.beta = dt / (4.0 * I.dx * I.dx);
+            b->classes.push_back(C);
+        } else {
+            c = it->second;
+        }
+        b->inst_class[i] = c;
+    }
+    const int n_cls = (int)b->classes.size();
+    // mask plateau [jm_lo, jm_hi] and table offsets
+    int64_t tab_total = 0;
+    int max_N = 0;
+    for (auto& C : b->classes) {
+        C.tab_off = tab_total;
+        tab_total += tab_doubles(C.N);
+        max_N = std::max(max_N, C.N);
+        C.jm_lo = 0;
+        C.jm_hi = C.N - 1;
+        if (b->mask_on) {
+            const double xb = 0.5 * C.N * C.dx - b->mask_width;
+            int lo_j = C.N, hi_j = -1;
+            for (int j = 0; j < C.N; ++j) {
+                const double x = (j - 0.5 * (C.N - 1)) * C.dx;
+                if (!(std::fabs(x) > xb)) {
+                    lo_j = std::min(lo_j, j);
+                    hi_j = std::max(hi_j, j);
+                }
+            }
+            C.jm_lo = lo_j;
+            C.jm_hi = hi_j;   // empty plateau (lo > hi) masks every point
+        }
+    }
+    // slots: instances ordered by class, then by decreasing Nt (long groups first); groups of 32
+    std::vector<int64_t> order(n_inst);
+    for (int64_t i = 0; i < n_inst; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t p, int64_t q) {
+        if (b->inst_class[p] != b->inst_class[q]) return b->inst_class[p] < b->inst_class[q];
+        return b->n_steps[p] > b->n_steps[q];
+    });
+    b->slot_of_inst.assign(n_inst, -1);
+    std::vector<int64_t> slot_row, slot_nt, slot_valid;
+    b->class_group_begin.assign(n_cls, 0);
+    b->class_group_end.assign(n_cls, 0);
+    int64_t psi_elems = 0;
+    for (int64_t k = 0; k < n_inst;) {
+        const int c = b->inst_class[order[k]];
+        b->class_group_begin[c] = (int64_t)b->groups.size();
+        while (k < n_inst && b->inst_class[order[k]] == c) {
+            GroupDesc G{};
+            G.cls = c;
+            G.N = b->classes[c].N;
+            G.slot0 = (int64_t)slot_row.size();
+            G.psi_off = psi_elems;
+            psi_elems += (int64_t)G.N * kLanes;
+            G.nt_max = 0;
+            for (int lane = 0; lane < kLanes; ++lane) {
+                if (k < n_inst && b->inst_class[order[k]] == c) {
+                    const int64_t i = order[k++];
+                    b->slot_of_inst[i] = (int64_t)slot_row.size();
+                    slot_row.push_back(b->row_off[i]);
+                    slot_nt.push_back(b->n_steps[i]);
+                    slot_valid.push_back(1);
+                    G.nt_max = std::max(G.nt_max, b->n_steps[i]);
+                } else {
+                    slot_row.push_back(0);
+                    slot_nt.push_back(-1);
+                    slot_valid.push_back(0);
+                }
+            }
+            b->groups.push_back(G);
+        }
+        b->class_group_end[c] = (int64_t)b->groups.size();
+    }
+    b->n_slots = (int64_t)slot_row.size();
+    b->psi_elems = psi_elems;
+
+    // device allocations
+    tdse_status st = TDSE_OK;
+    auto bail = [&](tdse_status s) {
+        free_device(b);
+        delete b;
+        return s;
+    };
+    cudaError_t e;
+    if ((e = dev_alloc(&b->d_cls, n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(classes)"));
+    if ((e = dev_alloc(&b->d_groups, b->groups.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(groups)"));
+    if ((e = dev_alloc(&b->d_tab, (size_t)tab_total)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(tables)"));
+    if ((e = dev_alloc(&b->d_slot_row, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
+    if ((e = dev_alloc(&b->d_slot_nt, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
+    if ((e = dev_alloc(&b->d_slot_valid, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
+    if ((e = dev_alloc(&b->d_psi, (size_t)psi_elems)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(psi)"));
+    if ((e = dev_alloc(&b->d_status, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(status)"));
+    int64_t gs_total = 0;
+    std::vector<int64_t> gs_off(n_cls);
+    for (int c = 0; c < n_cls; ++c) {
+        gs_off[c] = gs_total;
+        gs_total += 4 * (int64_t)b->classes[c].N;
+    }
+    if ((e = dev_alloc(&b->d_gs_work, (size_t)gs_total)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
+    if ((e = dev_alloc(&b->d_gs_off, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
+    if ((e = dev_alloc(&b->d_gs_energy, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
+    if ((e = dev_alloc(&b->d_gs_iters, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
+    if ((e = cudaMemcpy(b->d_cls, b->classes.data(), sizeof(ClassDesc) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_slot_row, slot_row.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_slot_nt, slot_nt.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_slot_valid, slot_valid.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_gs_off, gs_off.data(), sizeof(int64_t) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(b->d_status, 0, sizeof(int) * b->n_slots)) != cudaSuccess ||
+        (e = cudaMemset(b->d_psi, 0, sizeof(double2) * (size_t)std::max<int64_t>(psi_elems, 1))) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemcpy(setup)"));
+    if ((st = build_plan(b)) != TDSE_OK) return bail(st);
+    if ((e = launch_build_tables(b->d_cls, n_cls, max_N, dt, b->mask_width, b->mask_exp, b->mask_on, b->d_tab, 0)) != cudaSuccess)
+        return bail(cuda_fail(e, "build_tables launch"));
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "build_tables"));
+    *out = b;
+    return TDSE_OK;
+}
+
+void tdse_batch_destroy(tdse_batch* b)
+{
+    if (!b) return;
+    DeviceGuard guard(b->device);
+    cudaDeviceSynchronize();
+    free_device(b);
+    delete b;
+}
+
+tdse_status tdse_plan(const tdse_batch* b, tdse_plan_info* info)
+{
+    if (!b || !info) return fail(TDSE_ERR_ARG, "tdse_plan: NULL argument");
+    info->n_groups = (int64_t)b->groups.size();
+    info->segments = b->class_P.empty() ? 0 : *std::max_element(b->class_P.begin(), b->class_P.end());
+    info->halo = b->class_K.empty() ? 0 : *std::max_element(b->class_K.begin(), b->class_K.end());
+    info->scratch_bytes = b->scratch_elems * (int64_t)sizeof(double2);
+    info->psi_bytes = b->psi_elems * (int64_t)sizeof(double2);
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_segments(tdse_batch* b, int32_t segments)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_set_segments: NULL batch");
+    if (segments < 0 || segments > kMaxSegments) return fail(TDSE_ERR_ARG, "tdse_set_segments: out of [0, 16]");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    TDSE_CUDA(cudaDeviceSynchronize(), "tdse_set_segments: synchronize");
+    b->segments_override = segments;
+    return build_plan(b);
+}
+
+tdse_status tdse_ground_state(tdse_batch* b, double dtau, int64_t max_iter, double tol, double* energies_host,
+                              int64_t* iters_host, void* stream)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_ground_state: NULL batch");
+    if (!is_finite(dtau) || dtau <= 0.0) return fail(TDSE_ERR_ARG, "tdse_ground_state: dtau must be > 0");
+    if (max_iter < 1) return fail(TDSE_ERR_ARG, "tdse_ground_state: max_iter < 1");
+    if (!is_finite(tol) || tol < 0.0) return fail(TDSE_ERR_ARG, "tdse_ground_state: tol must be >= 0");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_cls = (int)b->classes.size();
+    TDSE_CUDA(launch_ground_state(b->d_cls, n_cls, (int)b->scheme, dtau, max_iter, tol, b->d_gs_work, b->d_gs_off,
+                                  b->d_gs_energy, b->d_gs_iters, st),
+              "ground_state launch");
+    TDSE_CUDA(launch_broadcast_psi(b->d_groups, (int64_t)b->groups.size(), b->d_gs_work, b->d_gs_off, b->d_slot_valid,
+                                   b->d_psi, st),
+              "broadcast launch");
+    b->initialized = true;
+    if (energies_host || iters_host) {
+        std::vector<double> e(n_cls);
+        std::vector<int64_t> it(n_cls);
+        TDSE_CUDA(cudaMemcpyAsync(e.data(), b->d_gs_energy, sizeof(double) * n_cls, cudaMemcpyDeviceToHost, st), "copy energies");
+        TDSE_CUDA(cudaMemcpyAsync(it.data(), b->d_gs_iters, sizeof(int64_t) * n_cls, cudaMemcpyDeviceToHost, st), "copy iters");
+        TDSE_CUDA(cudaStreamSynchronize(st), "ground_state");
+        for (int64_t i = 0; i < b->n_inst; ++i) {
+            if (energies_host) energies_host[i] = e[b->inst_class[i]];
+            if (iters_host) iters_host[i] = it[b->inst_class[i]];
+        }
+    }
+    return TDSE_OK;
+}
+
+tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, double* a_dev, int64_t sample_base,
+                           int64_t step_begin, int64_t step_end, void* stream)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_propagate: NULL batch");
+    if (!E_dev || !d_dev || !a_dev) return fail(TDSE_ERR_ARG, "tdse_propagate: NULL buffer");
+    if (step_begin < 0 || step_end < step_begin) return fail(TDSE_ERR_ARG, "tdse_propagate: bad step range");
+    if (sample_base < 0 || sample_base > step_begin) return fail(TDSE_ERR_ARG, "tdse_propagate: need 0 <= sample_base <= step_begin");
+    if (!b->initialized) return fail(TDSE_ERR_STATE, "tdse_propagate: no initial state (call tdse_ground_state or tdse_set_psi)");
+    for (int64_t i = 0; i < b->n_inst; ++i) {
+        const int64_t n_end = std::min(step_end, b->n_steps[i]);
+        int64_t top = -1;
+        if (step_begin == 0) top = 0;
+        if (n_end > step_begin) top = n_end;
+        if (top < 0) continue;
+        const int64_t len = b->row_off[i + 1] - b->row_off[i];
+        if (top - sample_base >= len)
+            return fail(TDSE_ERR_ARG, "tdse_propagate: row of instance " + std::to_string(i) + " too short for the step range");
+    }
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        const int64_t g0 = b->class_group_begin[c], g1 = b->class_group_end[c];
+        TDSE_CUDA(launch_propagate_fp64(b->d_groups, g0, g1 - g0, b->class_P[c], b->d_cls, b->d_tab, b->d_slot_row,
+                                        b->d_slot_nt, b->d_psi, b->d_scratch, E_dev, d_dev, a_dev, sample_base,
+                                        step_begin, step_end, b->mask_on, b->d_status, st),
+                  "propagate launch");
+    }
+    return TDSE_OK;
+}
+
+static tdse_status locate(const tdse_batch* b, int64_t inst, int64_t* off, int* N, int* lane)
+{
+    if (inst < 0 || inst >= b->n_inst) return fail(TDSE_ERR_ARG, "instance index out of range");
+    const int64_t slot = b->slot_of_inst[inst];
+    const GroupDesc& G = b->groups[slot / kLanes];
+    *off = G.psi_off;
+    *N = G.N;
+    *lane = (int)(slot % kLanes);
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_psi(tdse_batch* b, int64_t inst, double* psi_dev, void* stream)
+{
+    if (!b || !psi_dev) return fail(TDSE_ERR_ARG, "tdse_get_psi: NULL argument");
+    int64_t off;
+    int N, lane;
+    tdse_status s = locate(b, inst, &off, &N, &lane);
+    if (s != TDSE_OK) return s;
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    TDSE_CUDA(launch_get_psi(b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "get_psi launch");
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_psi(tdse_batch* b, int64_t inst, const double* psi_dev, void* stream)
+{
+    if (!b || !psi_dev) return fail(TDSE_ERR_ARG, "tdse_set_psi: NULL argument");
+    int64_t off;
+    int N, lane;
+    tdse_status s = locate(b, inst, &off, &N, &lane);
+    if (s != TDSE_OK) return s;
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    TDSE_CUDA(launch_set_psi(b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "set_psi launch");
+    b->initialized = true;
+    return TDSE_OK;
+}
+
+tdse_status tdse_check(tdse_batch* b, int64_t* first_bad, void* stream)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_check: NULL batch");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> flags((size_t)b->n_slots);
+    TDSE_CUDA(cudaMemcpyAsync(flags.data(), b->d_status, sizeof(int) * b->n_slots, cudaMemcpyDeviceToHost, st), "copy status");
+    TDSE_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int) * b->n_slots, st), "clear status");
+    TDSE_CUDA(cudaStreamSynchronize(st), "tdse_check");
+    int64_t bad = -1;
+    for (int64_t i = 0; i < b->n_inst && bad < 0; ++i)
+        if (flags[b->slot_of_inst[i]]) bad = i;
+    if (first_bad) *first_bad = bad;
+    if (bad >= 0) return fail(TDSE_ERR_NONFINITE, "instance " + std::to_string(bad) + ": norm non-finite or above 1 + 1e-6");
+    return TDSE_OK;
+}
+
+tdse_status tdse_spectrum(const double* a_dev, const int64_t* offsets_host, int64_t n_rows, double dt, int64_t k_begin,
+                          int64_t k_end, double* S_dev, void* stream)
+{
+    if (!a_dev || !offsets_host || !S_dev) return fail(TDSE_ERR_ARG, "tdse_spectrum: NULL argument");
+    if (n_rows < 1 || n_rows > (int64_t(1) << 31)) return fail(TDSE_ERR_ARG, "tdse_spectrum: n_rows out of range");
+    if (k_begin < 0 || k_end <= k_begin) return fail(TDSE_ERR_ARG, "tdse_spectrum: need 0 <= k_begin < k_end");
+    if (!is_finite(dt)) return fail(TDSE_ERR_ARG, "tdse_spectrum: dt not finite");
+    for (int64_t r = 0; r < n_rows; ++r)
+        if (offsets_host[r + 1] < offsets_host[r] || offsets_host[r] < 0)
+            return fail(TDSE_ERR_ARG, "tdse_spectrum: offsets must be non-decreasing and >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t* d_off = nullptr;
+    TDSE_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_off), sizeof(int64_t) * (n_rows + 1), st), "cudaMallocAsync(offsets)");
+    cudaError_t e = cudaMemcpyAsync(d_off, offsets_host, sizeof(int64_t) * (n_rows + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_spectrum(a_dev, d_off, n_rows, dt, k_begin, k_end, S_dev, st);
+    cudaError_t e2 = cudaFreeAsync(d_off, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tdse_spectrum");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "tdse_spectrum free");
+    return TDSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,231 @@
+"""Thin ctypes binding of libtdse.so (C ABI in include/tdse.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA kernels.  Device
+buffers are torch tensors (float64, contiguous, on the batch's device); host arrays are numpy.
+There is no CPU fallback: ``load()`` raises if the library is missing or cannot be opened.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+TDSE_OK, TDSE_ERR_ARG, TDSE_ERR_CUDA, TDSE_ERR_NONFINITE, TDSE_ERR_TIMEOUT, TDSE_ERR_NOMEM, TDSE_ERR_STATE = range(7)
+TDSE_FP64, TDSE_MIXED = 0, 1
+TDSE_FULL_CN, TDSE_NUMEROV_SPLIT = 0, 1
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtdse.so")
+_lib = None
+
+#: C-ABI entry points declared in include/tdse.h
+EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
+           "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_segments", "tdse_last_error")
+
+
+class tdse_instance(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("dx", ctypes.c_double), ("softening", ctypes.c_double),
+                ("charge", ctypes.c_double)]
+
+
+class tdse_absorber(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_double), ("exponent", ctypes.c_double)]
+
+
+class tdse_plan_info(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int64), ("segments", ctypes.c_int32), ("halo", ctypes.c_int32),
+                ("scratch_bytes", ctypes.c_int64), ("psi_bytes", ctypes.c_int64)]
+
+
+class TDSEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("tdse status %d: %s" % (status, msg))
+        self.status = status
+
+
+_vp, _dp, _i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+
+
+def load(path: str | None = None):
+    """Open libtdse.so and declare the C signatures.  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libtdse.so is not built (expected at %s): run __graft_entry__.build()" % p)
+    L = ctypes.CDLL(p)
+    L.tdse_batch_create.argtypes = [ctypes.POINTER(tdse_instance), ctypes.c_int64, ctypes.c_double, _i64p, _i64p,
+                                    ctypes.POINTER(tdse_absorber), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(_vp)]
+    L.tdse_batch_destroy.argtypes = [_vp]
+    L.tdse_batch_destroy.restype = None
+    L.tdse_ground_state.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_double, _dp, _i64p, _vp]
+    L.tdse_propagate.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp]
+    L.tdse_get_psi.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
+    L.tdse_set_psi.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
+    L.tdse_check.argtypes = [_vp, _i64p, _vp]
+    L.tdse_spectrum.argtypes = [_vp, _i64p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _vp, _vp]
+    L.tdse_plan.argtypes = [_vp, ctypes.POINTER(tdse_plan_info)]
+    L.tdse_set_segments.argtypes = [_vp, ctypes.c_int32]
+    L.tdse_last_error.argtypes = []
+    L.tdse_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("tdse_batch_destroy", "tdse_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != TDSE_OK:
+        raise TDSEError(rc, load().tdse_last_error().decode())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------------- C-ABI mirrors
+
+def tdse_batch_create(inst, n_steps, row_offsets, dt, absorber=(20.0, 0.125), precision=TDSE_FP64,
+                      scheme=TDSE_FULL_CN, device=0):
+    """inst: sequence of (N, dx, softening, charge); returns the opaque handle."""
+    L = load()
+    n = len(inst)
+    arr = (tdse_instance * n)(*[tdse_instance(int(a), float(b), float(c), float(d)) for a, b, c, d in inst])
+    ns = np.ascontiguousarray(n_steps, dtype=np.int64)
+    ro = np.ascontiguousarray(row_offsets, dtype=np.int64)
+    if ns.size != n or ro.size != n + 1:
+        raise ValueError("n_steps needs n entries and row_offsets n + 1")
+    ab = None if absorber is None else ctypes.byref(tdse_absorber(float(absorber[0]), float(absorber[1])))
+    h = _vp()
+    _check(L.tdse_batch_create(arr, n, float(dt), ns.ctypes.data_as(_i64p), ro.ctypes.data_as(_i64p), ab,
+                               int(precision), int(scheme), int(device), ctypes.byref(h)))
+    return h
+
+
+def tdse_batch_destroy(h):
+    load().tdse_batch_destroy(h)
+
+
+def tdse_last_error():
+    return load().tdse_last_error().decode()
+
+
+class Batch:
+    """A batch of independent TDSE instances living on one GPU (see include/tdse.h)."""
+
+    def __init__(self, N, dx, softening, n_steps, dt, charge=1.0, row_offsets=None, absorber=(20.0, 0.125),
+                 precision=TDSE_FP64, scheme=TDSE_FULL_CN, device=0):
+        N = np.atleast_1d(np.asarray(N, dtype=np.int64))
+        n = N.size
+        dx = np.broadcast_to(np.asarray(dx, dtype=np.float64), (n,))
+        a = np.broadcast_to(np.asarray(softening, dtype=np.float64), (n,))
+        Z = np.broadcast_to(np.asarray(charge, dtype=np.float64), (n,))
+        self.n_steps = np.broadcast_to(np.asarray(n_steps, dtype=np.int64), (n,)).copy()
+        if row_offsets is None:
+            row_offsets = np.concatenate([[0], np.cumsum(self.n_steps + 1)])
+        self.row_offsets = np.ascontiguousarray(row_offsets, dtype=np.int64)
+        self.N = N
+        self.dx = np.array(dx)
+        self.dt = float(dt)
+        self.device = int(device)
+        self.n_inst = n
+        self._h = tdse_batch_create(list(zip(N, dx, a, Z)), self.n_steps, self.row_offsets, dt, absorber, precision,
+                                    scheme, device)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            tdse_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def ground_state(self, dtau=0.1, max_iter=20000, tol=1e-13, stream=None):
+        e = np.zeros(self.n_inst)
+        it = np.zeros(self.n_inst, dtype=np.int64)
+        _check(load().tdse_ground_state(self._h, float(dtau), int(max_iter), float(tol), e.ctypes.data_as(_dp),
+                                        it.ctypes.data_as(_i64p), _stream_ptr(stream)))
+        return e, it
+
+    def propagate(self, E, d, a, step_begin=0, step_end=None, sample_base=0, stream=None):
+        """Device tensors E, d, a laid out by row_offsets (see tdse_propagate).  CPU tensors are
+        copied to the device before and the outputs back after the call (end-to-end use)."""
+        import torch
+        if step_end is None:
+            step_end = int(self.n_steps.max())
+        host = not E.is_cuda
+        if host:
+            dev = torch.device("cuda", self.device)
+            Ed = E.to(dev, non_blocking=True)
+            dd = torch.empty(d.shape, dtype=torch.float64, device=dev)
+            ad = torch.empty(a.shape, dtype=torch.float64, device=dev)
+        else:
+            Ed, dd, ad = E, d, a
+        _check(load().tdse_propagate(self._h, _dev_ptr(Ed, "E"), _dev_ptr(dd, "d"), _dev_ptr(ad, "a"),
+                                     int(sample_base), int(step_begin), int(step_end), _stream_ptr(stream)))
+        if host:
+            d.copy_(dd, non_blocking=True)
+            a.copy_(ad, non_blocking=True)
+
+    def get_psi(self, inst, stream=None):
+        import torch
+        out = torch.empty(2 * int(self.N[inst]), dtype=torch.float64, device=torch.device("cuda", self.device))
+        _check(load().tdse_get_psi(self._h, int(inst), _dev_ptr(out, "psi"), _stream_ptr(stream)))
+        return torch.view_as_complex(out.view(-1, 2))
+
+    def set_psi(self, inst, psi, stream=None):
+        import torch
+        t = torch.view_as_real(psi.to(torch.complex128).contiguous()).reshape(-1).contiguous()
+        if t.numel() != 2 * int(self.N[inst]):
+            raise ValueError("psi must have N complex entries")
+        _check(load().tdse_set_psi(self._h, int(inst), _dev_ptr(t, "psi"), _stream_ptr(stream)))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def check(self, stream=None):
+        bad = ctypes.c_int64(-1)
+        rc = load().tdse_check(self._h, ctypes.byref(bad), _stream_ptr(stream))
+        if rc == TDSE_ERR_NONFINITE:
+            return int(bad.value)
+        _check(rc)
+        return -1
+
+    def plan(self):
+        info = tdse_plan_info()
+        _check(load().tdse_plan(self._h, ctypes.byref(info)))
+        return dict(n_groups=info.n_groups, segments=info.segments, halo=info.halo,
+                    scratch_bytes=info.scratch_bytes, psi_bytes=info.psi_bytes)
+
+    def set_segments(self, segments):
+        _check(load().tdse_set_segments(self._h, int(segments)))
+
+
+def spectrum(a, offsets, dt, k_begin, k_end, out=None, stream=None):
+    """S[r, k - k_begin] = dt^2 |DFT of row r at bin k|^2 (see tdse_spectrum); a is a device tensor."""
+    import torch
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    n_rows = offs.size - 1
+    if out is None:
+        out = torch.empty((n_rows, k_end - k_begin), dtype=torch.float64, device=a.device)
+    _check(load().tdse_spectrum(_dev_ptr(a, "a"), offs.ctypes.data_as(_i64p), n_rows, float(dt), int(k_begin),
+                                int(k_end), _dev_ptr(out, "S"), _stream_ptr(stream)))
+    return out

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every entry point of include/tdse.h; host-side
+argument validation rejects bad calls before any CUDA work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_04115_gb300 import build, tdse
+    build.build()
+    return tdse.load()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(tdse_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2507_04115_gb300 import tdse
+    declared = _declared()
+    assert declared, "no entry points found in include/"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(tdse.EXPORTS) | (declared - set(tdse.EXPORTS))
+    assert set(tdse.EXPORTS) <= declared
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib):
+    from paper_2507_04115_gb300 import tdse
+    good = [(256, 0.2, 1.2, 1.0)]
+    bad_cases = [
+        dict(inst=[(8, 0.2, 1.2, 1.0)]),                 # N too small
+        dict(inst=[(256, -0.2, 1.2, 1.0)]),              # dx <= 0
+        dict(inst=[(256, 0.2, 0.0, 1.0)]),               # softening <= 0
+        dict(dt=0.0),                                    # dt == 0
+        dict(n_steps=[-1]),                              # negative steps
+        dict(row_offsets=[5, 2]),                        # decreasing offsets
+        dict(precision=7),                               # unknown precision
+    ]
+    for case in bad_cases:
+        kw = dict(inst=good, n_steps=[10], row_offsets=[0, 11], dt=0.05)
+        kw.update(case)
+        with pytest.raises(tdse.TDSEError) as ei:
+            tdse.tdse_batch_create(kw["inst"], kw["n_steps"], kw["row_offsets"], kw["dt"],
+                                   precision=kw.get("precision", tdse.TDSE_FP64))
+        assert ei.value.status == tdse.TDSE_ERR_ARG, case
+        assert tdse.tdse_last_error()
+
+
+def test_null_handles_are_rejected(lib):
+    from paper_2507_04115_gb300 import tdse
+    assert lib.tdse_propagate(None, None, None, None, 0, 0, 1, None) == tdse.TDSE_ERR_ARG
+    assert lib.tdse_ground_state(None, 0.1, 10, 1e-12, None, None, None) == tdse.TDSE_ERR_ARG
+    assert lib.tdse_get_psi(None, 0, None, None) == tdse.TDSE_ERR_ARG
+    info = tdse.tdse_plan_info()
+    assert lib.tdse_plan(None, ctypes.byref(info)) == tdse.TDSE_ERR_ARG
+    offs = np.array([0, 4], dtype=np.int64)
+    assert lib.tdse_spectrum(None, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1, 0.1, 0, 2, None,
+                             None) == tdse.TDSE_ERR_ARG
+    lib.tdse_batch_destroy(None)
+
+
+def test_package_import_does_not_load_library():
+    import importlib
+    import paper_2507_04115_gb300
+    importlib.reload(paper_2507_04115_gb300)
+    from paper_2507_04115_gb300 import inputs
+    assert inputs.pulse_steps(4, 0.057, 0.05) == 8818

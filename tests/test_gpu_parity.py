@@ -1,0 +1,283 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance (FP64 path).  Both sides evaluate the same discrete scheme in IEEE double; they differ
+only in the order of rounding (midpoint-free CN update 2y - psi, fused multiply-adds, the
+refined hardware reciprocal, the halo-truncated sweeps whose truncation is < 1e-18 of max|psi|).
+Crank-Nicolson is unitary, so rounding differences add up like a random walk and do not grow
+exponentially: after 1e5 steps they stay near 1e-16 * sqrt(1e5) * (condition of the observable)
+~ 1e-12 relative to max|d|, max|a|.  The tests allow 1e-9 relative to the signal's maximum, three
+orders of magnitude above that estimate and far below any physical effect; spectra must agree to
+1e-6 relative (the stated bound) on every bin whose power is above 1e-14 of the peak.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL_SERIES = 1e-9
+# A fixed iteration count (tol = 0) makes the GPU and the oracle take exactly the same number of
+# imaginary-time steps, so their ground states agree to rounding (with a stopping tolerance the two
+# may stop one iteration apart, and the wavefunction converges only like sqrt of the energy).
+GS_KW = dict(dtau=0.1, max_iter=1500, tol=0.0)
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_04115_gb300 import build, tdse
+    build.build()
+    tdse.load()
+    import oracle
+    oracle.build()
+    return tdse, oracle
+
+
+def _rel(x, ref, floor=1e-6):
+    """max |x - ref| / max(max |ref|, floor): the floor keeps rounding-level signals (a field-free
+    instance has <x> ~ 1e-16) from turning absolute agreement into a large relative number."""
+    return float(np.max(np.abs(np.asarray(x) - np.asarray(ref))) / max(np.max(np.abs(ref)), floor))
+
+
+def _device_rows(rows, offs, dev):
+    E = np.zeros(int(offs[-1]))
+    for i, r in enumerate(rows):
+        E[offs[i]: offs[i] + r.size] = r
+    return torch.from_numpy(E).to(dev)
+
+
+def test_ground_state_matches_oracle(env):
+    """Fixed iteration count: the wavefunctions agree to rounding.  With the stopping tolerance the
+    energies agree to 1e-12 and the iteration counts to within one."""
+    tdse, oracle = env
+    for N, dx, a in [(2000, 0.2, 1.1901733590266939), (4096, 0.15, 1.19), (300, 0.25, 2.0)]:
+        b = tdse.Batch([N], dx, a, [1], 0.05)
+        e, it = b.ground_state(**GS_KW)
+        psi_o, e_o, it_o = oracle.ground_state(N, dx, a, **GS_KW)
+        assert abs(e[0] - e_o) < 1e-13 and int(it[0]) == it_o == GS_KW["max_iter"]
+        psi = b.get_psi(0).cpu().numpy()
+        assert np.max(np.abs(psi - psi_o)) < 1e-12
+        e, it = b.ground_state(dtau=0.1, tol=1e-13)
+        psi_o, e_o, it_o = oracle.ground_state(N, dx, a, dtau=0.1, tol=1e-13)
+        assert abs(e[0] - e_o) < 1e-12
+        assert abs(int(it[0]) - it_o) <= 1
+        b.close()
+
+
+def test_single_atom_full_propagation(env):
+    """The single-atom workload (N = 2000, 8818 steps, mask on) end to end: d, a and |DFT(a)|^2."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    wl = inputs.single_atom()
+    N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+    a = oracle.fit_softening(wl.target_energy, N, dx)
+    E = wl.field_rows()[0]
+    b = tdse.Batch([N], dx, a, [E.size - 1], dt, absorber=(wl.mask_width, wl.mask_exponent))
+    b.ground_state(**GS_KW)
+    dev = torch.device("cuda", 0)
+    Et = torch.from_numpy(E).to(dev)
+    d = torch.zeros_like(Et)
+    acc = torch.zeros_like(Et)
+    b.propagate(Et, d, acc)
+    torch.cuda.synchronize()
+    assert b.check() == -1
+    psi0, _, _ = oracle.ground_state(N, dx, a, **GS_KW)
+    _, d_o, a_o = oracle.propagate(psi0, E, dx, dt, a, mask_values=oracle.mask(N, dx, wl.mask_width, wl.mask_exponent))
+    assert _rel(d.cpu().numpy(), d_o) < RTOL_SERIES
+    assert _rel(acc.cpu().numpy(), a_o) < RTOL_SERIES
+    S = tdse.spectrum(acc, [0, E.size], dt, 0, E.size).cpu().numpy()[0]
+    S_o = oracle.spectrum(a_o, dt)
+    keep = S_o > 1e-14 * S_o.max()
+    assert np.max(np.abs(S[keep] - S_o[keep]) / S_o[keep]) < 1e-6
+    b.close()
+
+
+def test_ragged_batch_chunks_classes_and_segments(env):
+    """Ragged batch: 45 instances (not a multiple of 32), three grid classes, uneven Nt (including 0),
+    chunked calls with a moving sample_base, and every segment count the planner allows."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    rng = np.random.default_rng(11)
+    n = 45
+    classes = [(384, 0.2, 1.19), (512, 0.15, 1.3), (640, 0.2, 1.0)]
+    cls = rng.integers(0, 3, n)
+    N = np.array([classes[c][0] for c in cls])
+    dx = np.array([classes[c][1] for c in cls])
+    soft = np.array([classes[c][2] for c in cls])
+    dt = 0.05
+    nt = rng.integers(150, 420, n)
+    nt[3] = 0
+    rows = [inputs.sin2_pulse(int(k), dt, rng.uniform(0.04, 0.1), 0.057, 1.0, rng.uniform(0, 6)) for k in nt]
+    offs = np.concatenate([[0], np.cumsum(nt + 1)])
+    dev = torch.device("cuda", 0)
+    Et = _device_rows(rows, offs, dev)
+    refs = []
+    for i in range(n):
+        psi0, _, _ = oracle.ground_state(int(N[i]), dx[i], soft[i], **GS_KW)
+        m = oracle.mask(int(N[i]), dx[i], 20.0, 0.125)
+        refs.append(oracle.propagate(psi0, rows[i], dx[i], dt, soft[i], mask_values=m)[1:])
+    b = tdse.Batch(N, dx, soft, nt, dt, row_offsets=offs, absorber=(20.0, 0.125))
+    for P in (1, 2, 3, 0):
+        b.set_segments(P)
+        b.ground_state(**GS_KW)
+        d = torch.full_like(Et, np.nan)
+        acc = torch.full_like(Et, np.nan)
+        b.propagate(Et, d, acc, 0, 100)
+        b.propagate(Et, d, acc, 100, 260)
+        b.propagate(Et, d, acc, 260, 1000)
+        torch.cuda.synchronize()
+        assert b.check() == -1
+        dh, ah = d.cpu().numpy(), acc.cpu().numpy()
+        for i in range(n):
+            sl = slice(offs[i], offs[i + 1])
+            assert _rel(dh[sl], refs[i][0]) < RTOL_SERIES, (P, i)
+            assert _rel(ah[sl], refs[i][1]) < RTOL_SERIES, (P, i)
+    b.close()
+
+
+def test_chunk_with_sample_base_streaming(env):
+    """Chunk buffers holding only the samples of each call (sample_base = step_begin)."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    N, dx, a, dt, nt = 512, 0.2, 1.19, 0.05, 400
+    n = 3
+    rows = [inputs.sin2_pulse(nt, dt, 0.05 + 0.01 * i, 0.057, 1.0, 0.5 * i) for i in range(n)]
+    C = 128
+    b = tdse.Batch([N] * n, dx, a, [nt] * n, dt, row_offsets=np.arange(n + 1) * (C + 1), absorber=(20.0, 0.125))
+    b.ground_state(**GS_KW)
+    dev = torch.device("cuda", 0)
+    d_all = np.zeros((n, nt + 1))
+    a_all = np.zeros((n, nt + 1))
+    for s0 in range(0, nt, C):
+        s1 = min(nt, s0 + C)
+        Ec = torch.zeros(n * (C + 1), dtype=torch.float64, device=dev)
+        for i in range(n):
+            Ec[i * (C + 1): i * (C + 1) + s1 - s0 + 1] = torch.from_numpy(rows[i][s0: s1 + 1])
+        dc = torch.zeros_like(Ec)
+        ac = torch.zeros_like(Ec)
+        b.propagate(Ec, dc, ac, s0, s1, sample_base=s0)
+        dch, ach = dc.cpu().numpy(), ac.cpu().numpy()
+        for i in range(n):
+            lo = 0 if s0 == 0 else 1
+            d_all[i, s0 + lo: s1 + 1] = dch[i * (C + 1) + lo: i * (C + 1) + s1 - s0 + 1]
+            a_all[i, s0 + lo: s1 + 1] = ach[i * (C + 1) + lo: i * (C + 1) + s1 - s0 + 1]
+    psi0, _, _ = oracle.ground_state(N, dx, a, **GS_KW)
+    m = oracle.mask(N, dx, 20.0, 0.125)
+    for i in range(n):
+        _, d_o, a_o = oracle.propagate(psi0, rows[i], dx, dt, a, mask_values=m)
+        assert _rel(d_all[i], d_o) < RTOL_SERIES
+        assert _rel(a_all[i], a_o) < RTOL_SERIES
+    b.close()
+
+
+def test_volume_batch_full_size_sampled(env):
+    """The 8192 x 4096 volume batch at full size with the default plan the benchmark uses, for the
+    first 600 steps; eight sampled instances checked one by one against the oracle."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    wl = inputs.volume_batch()
+    N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+    a = oracle.fit_softening(wl.target_energy, N, dx)
+    steps = 600
+    dev = torch.device("cuda", 0)
+    n = wl.n_inst
+    E = torch.empty((n, steps + 1), dtype=torch.float64, device=dev)
+    inputs.sin2_pulse_batch(steps, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
+    b = tdse.Batch([N] * n, dx, a, [steps] * n, dt, absorber=(wl.mask_width, wl.mask_exponent))
+    plan = b.plan()
+    assert plan["n_groups"] == n // 32
+    b.ground_state(**GS_KW)
+    Ef = E.reshape(-1).contiguous()
+    d = torch.zeros_like(Ef)
+    acc = torch.zeros_like(Ef)
+    b.propagate(Ef, d, acc, 0, steps)
+    torch.cuda.synchronize()
+    assert b.check() == -1
+    psi0, _, _ = oracle.ground_state(N, dx, a, **GS_KW)
+    m = oracle.mask(N, dx, wl.mask_width, wl.mask_exponent)
+    dh = d.view(n, steps + 1).cpu().numpy()
+    ah = acc.view(n, steps + 1).cpu().numpy()
+    Eh = E.cpu().numpy()
+    for i in inputs.subsample(n, 8, 101):
+        _, d_o, a_o = oracle.propagate(psi0, Eh[i], dx, dt, a, mask_values=m)
+        assert _rel(dh[i], d_o) < RTOL_SERIES, i
+        assert _rel(ah[i], a_o) < RTOL_SERIES, i
+    b.close()
+
+
+def test_batch_position_invariance(env):
+    """An instance gives bit-identical results whatever its slot, batch size or neighbours."""
+    tdse, _ = env
+    from paper_2507_04115_gb300 import inputs
+    N, dx, a, dt, nt = 512, 0.2, 1.19, 0.05, 300
+    E1 = inputs.sin2_pulse(nt, dt, 0.07, 0.057, 1.0, 0.2)
+    dev = torch.device("cuda", 0)
+    outs = []
+    for n, pos in [(1, 0), (40, 17), (70, 63)]:
+        rows = [inputs.sin2_pulse(nt, dt, 0.03 + 0.001 * i, 0.057, 1.0, 0.0) for i in range(n)]
+        rows[pos] = E1
+        offs = np.arange(n + 1) * (nt + 1)
+        b = tdse.Batch([N] * n, dx, a, [nt] * n, dt, absorber=(20.0, 0.125))
+        b.set_segments(2)
+        b.ground_state(**GS_KW)
+        Et = _device_rows(rows, offs, dev)
+        d = torch.zeros_like(Et)
+        acc = torch.zeros_like(Et)
+        b.propagate(Et, d, acc)
+        outs.append((d[offs[pos]: offs[pos + 1]].cpu().numpy(), acc[offs[pos]: offs[pos + 1]].cpu().numpy()))
+        b.close()
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+
+
+def test_psi_roundtrip_resume_and_nonfinite_flag(env):
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    N, dx, a, dt, nt = 256, 0.2, 1.19, 0.05, 200
+    dev = torch.device("cuda", 0)
+    b = tdse.Batch([N, N], dx, a, [nt, nt], dt, absorber=None)
+    with pytest.raises(tdse.TDSEError) as ei:
+        z = torch.zeros(2 * (nt + 1), dtype=torch.float64, device=dev)
+        b.propagate(z, z.clone(), z.clone())
+    assert ei.value.status == tdse.TDSE_ERR_STATE
+    b.ground_state(tol=1e-13)
+    psi = b.get_psi(1)
+    b.set_psi(0, psi * np.exp(0.3j))
+    assert torch.allclose(b.get_psi(0), psi * np.exp(0.3j), atol=0, rtol=0)
+    E = inputs.sin2_pulse(nt, dt, 0.05, 0.057, 1.0)
+    Et = torch.from_numpy(np.concatenate([E, E])).to(dev)
+    Et[nt + 1 + 50] = float("nan")
+    d = torch.zeros_like(Et)
+    acc = torch.zeros_like(Et)
+    b.propagate(Et, d, acc)
+    assert b.check() == 1
+    assert b.check() == -1          # flags cleared
+    b.close()
+    # rows too short for the requested step range are rejected on the host, before any launch
+    short = tdse.Batch([N, N], dx, a, [nt, nt], dt, row_offsets=[0, 100, 200], absorber=None)
+    short.ground_state(tol=1e-13)
+    with pytest.raises(tdse.TDSEError) as ei:
+        short.propagate(Et, d, acc, 0, nt)
+    assert ei.value.status == tdse.TDSE_ERR_ARG
+    short.propagate(Et, d, acc, 0, 99)      # fits: samples 0..99 of each 100-sample row
+    torch.cuda.synchronize()
+    short.close()
+
+
+def test_spectrum_kernel_matches_fft(env):
+    tdse, oracle = env
+    rng = np.random.default_rng(3)
+    lens = [1, 7, 64, 1000, 4097]
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    data = rng.standard_normal(offs[-1])
+    a = torch.from_numpy(data).cuda()
+    kmax = max(lens)
+    S = tdse.spectrum(a, offs, 0.02, 0, kmax).cpu().numpy()
+    for r, L in enumerate(lens):
+        ref = oracle.spectrum(data[offs[r]: offs[r + 1]], 0.02)
+        k = np.arange(kmax)
+        expect = ref[k % L]
+        assert np.max(np.abs(S[r] - expect)) <= 1e-9 * max(expect.max(), 1e-300) + 1e-18
+    S2 = tdse.spectrum(a, offs, 0.02, 5, 9).cpu().numpy()
+    assert np.array_equal(S2, S[:, 5:9])
