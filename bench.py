@@ -42,7 +42,7 @@ FP64_FMA_PER_CLK_PER_SM = 2.0        # GB300 FP64 pipe: 2 FMA/clk/SM (1.2 TFLOP/
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_propagate_fp64_volume_traffic.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_2507_04115_gb300", "csrc", "tdse_kernels.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2507_04115_gb300", "csrc", "tdse_propagate.cu")
 
 
 def parse_args():
@@ -55,7 +55,11 @@ def parse_args():
     p.add_argument("--cpu-baseline", type=int, default=1, help="time the oracle on the host cores (rank 0, N = 1)")
     p.add_argument("--cpu-instances", type=int, default=0, help="oracle sample size (0 = one per core, max 16)")
     p.add_argument("--ref-steps-per-step", type=int, default=8192, help="oracle time steps per reference step")
-    p.add_argument("--segments", type=int, default=0, help="override the planner's segments per instance")
+    p.add_argument("--warps", type=int, default=0, help="override warps per CTA (segments per instance)")
+    p.add_argument("--ctas-per-sm", type=int, default=0, help="override CTAs per SM of the persistent grid")
+    p.add_argument("--slice", type=int, default=0, help="override time steps per scheduling slice")
+    p.add_argument("--instances", type=int, default=8192, help="instances per GPU (smaller = profiling case)")
+    p.add_argument("--nt", type=int, default=0, help="propagate only the first nt steps (0 = whole pulse)")
     return p.parse_args()
 
 
@@ -185,10 +189,10 @@ def own_arm(args):
 
     # weak scaling: rank r owns its own 64 x 128 slice of a (64 x 128 world)-point volume
     full = inputs.gaussian_beam_volume(n_z=128 * world) if world > 1 else inputs.volume_batch()
-    n = 8192
-    sl = slice(rank * n, (rank + 1) * n)
+    n = min(args.instances, 8192)
+    sl = slice(rank * 8192, rank * 8192 + n)
     N, dx, dt = int(full.N[0]), float(full.dx[0]), full.dt
-    Nt = int(full.n_steps[0])
+    Nt = int(full.n_steps[0]) if args.nt <= 0 else min(args.nt, int(full.n_steps[0]))
     omega, ncyc = float(full.omega[0]), float(full.n_cycles[0])
     E0, phi = full.E0[sl], full.phi[sl]
     n_chunks = args.warmup + args.steps
@@ -220,8 +224,8 @@ def own_arm(args):
     offs = np.arange(n + 1, dtype=np.int64) * (S + 1)
     batch = tdse.Batch([N] * n, dx, a_soft, [Nt] * n, dt, row_offsets=offs,
                        absorber=(full.mask_width, full.mask_exponent), device=local_rank)
-    if args.segments:
-        batch.set_segments(args.segments)
+    if args.warps or args.ctas_per_sm or args.slice:
+        batch.set_launch(args.warps, args.ctas_per_sm, args.slice)
     plan = batch.plan()
     stream = torch.cuda.current_stream(dev)
 
@@ -377,7 +381,9 @@ def own_arm(args):
                       "l2": "inputs larger than L2: psi %.0f MB + scratch %.0f MB per GPU" %
                             (plan["psi_bytes"] / 1e6, plan["scratch_bytes"] / 1e6),
                       "precision": "fp64", "scheme": "full_cn", "segments": plan["segments"],
-                      "halo": plan["halo"], "parallelism": "instances sharded over GPUs, no collective"},
+                      "halo": plan["halo"], "warps_per_cta": plan["warps_per_cta"], "ctas": plan["ctas"],
+                      "slice_steps": plan["slice_steps"],
+                      "parallelism": "instances sharded over GPUs, no collective"},
            "solves_per_s": value / (N * Nt),
            "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clk,
            "gpu_launches": args.steps, "nonfinite_instance": bad,

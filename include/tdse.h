@@ -49,7 +49,8 @@ typedef enum {
     TDSE_OK = 0,
     TDSE_ERR_ARG = 1,        /* invalid argument; nothing was launched */
     TDSE_ERR_CUDA = 2,       /* a CUDA runtime call failed */
-    TDSE_ERR_NONFINITE = 3,  /* an instance's norm became non-finite or grew above 1 + 1e-6 */
+    TDSE_ERR_NONFINITE = 3,  /* an instance's norm became non-finite or grew above 1 + 1e-6 (FP64),
+                                1 + 1e-3 (MIXED) */
     TDSE_ERR_TIMEOUT = 4,    /* reserved: a bounded device wait gave up */
     TDSE_ERR_NOMEM = 5,      /* device or host allocation failed */
     TDSE_ERR_STATE = 6       /* call out of order (e.g. propagate before any initial state) */
@@ -57,8 +58,8 @@ typedef enum {
 
 typedef enum {
     TDSE_FP64 = 0,   /* all arithmetic and storage in IEEE double */
-    TDSE_MIXED = 1   /* psi and potential/field arithmetic in float; elimination coefficients and
-                        observable accumulation in double (reserved in this version) */
+    TDSE_MIXED = 1   /* psi, the solve's right-hand side and back substitution in float; the
+                        elimination recurrence (pivots) and the observable sums in double */
 } tdse_precision;
 
 typedef enum {
@@ -132,7 +133,8 @@ tdse_status tdse_get_psi(tdse_batch* batch, int64_t inst, double* psi_dev, void*
 tdse_status tdse_set_psi(tdse_batch* batch, int64_t inst, const double* psi_dev, void* stream);
 
 /* Synchronise the stream and report TDSE_ERR_NONFINITE if any instance's norm became non-finite
- * or exceeded 1 + 1e-6 during a propagation since the batch was created or last checked;
+ * or exceeded 1 + 1e-6 (FP64; 1 + 1e-3 in MIXED) during a propagation since the batch was created
+ * or last checked;
  * *first_bad_host (may be NULL) receives the first such instance or -1.  Clears the flags. */
 tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream);
 
@@ -146,21 +148,30 @@ tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream)
 tdse_status tdse_spectrum(const double* a_dev, const int64_t* offsets_host, int64_t n_rows, double dt,
                           int64_t k_begin, int64_t k_end, double* S_dev, void* stream);
 
-/* Plan chosen for the batch (for benchmarks and tests): number of 32-instance groups, warps per
- * instance (segments), halo length in points, scratch bytes, and wavefunction bytes. */
+/* Plan chosen for the batch (for benchmarks and tests): number of 32-instance groups, grid
+ * segments per instance (largest over the classes), halo length in points (largest), warps per
+ * CTA, CTAs of the persistent propagation grid, time steps per scheduling slice, and the bytes of
+ * the propagation scratch and of the wavefunctions. */
 typedef struct {
     int64_t n_groups;
     int32_t segments;
     int32_t halo;
+    int32_t warps_per_cta;
+    int32_t ctas;
+    int32_t slice_steps;
     int64_t scratch_bytes;
     int64_t psi_bytes;
 } tdse_plan_info;
 
 tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);
 
-/* Override the number of segments (warps) per instance for later calls; 0 restores the
- * default.  The value is clamped to what the grid and the halo allow; the scratch is resized. */
-tdse_status tdse_set_segments(tdse_batch* batch, int32_t segments);
+/* Override the launch configuration for later calls (0 keeps the default of each):
+ * warps_per_cta in [1, 16] (default 8; also the largest number of segments per instance),
+ * ctas_per_sm in [1, 32] (default 1; clamped to the occupancy limit), slice_steps >= 1 (default 16),
+ * max_ctas >= 1 caps the persistent grid (default: no cap beyond SMs x ctas_per_sm and the number
+ * of groups).  Synchronises the device; the scratch is reallocated. */
+tdse_status tdse_set_launch(tdse_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
+                            int32_t max_ctas);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* tdse_last_error(void);

@@ -13,6 +13,9 @@ Contents
     the sentence after Eq. "SC potential"), by a bracketing root finder;
   * ``propagate_many``: one oracle instance per worker process (spawned), for baselines.
 
+``adjoint``: the exact discrete adjoint of the FULL_CN forward map (gradient of a loss of d and a
+with respect to every field sample).
+
 Scheme ids: 0 = FULL_CN (E in the diagonal at the midpoint field), 1 = NUMEROV_SPLIT
 (the paper's Eqs. "CN - step 4/2/3").
 """
@@ -59,7 +62,10 @@ def lib():
         L.oracle_propagate.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_long, ctypes.c_long,
                                        _dp, _dp, _dp]
-        for f in (L.oracle_grid, L.oracle_mask, L.oracle_energy, L.oracle_ground_state, L.oracle_propagate):
+        L.oracle_adjoint.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     _dp, _dp, ctypes.c_long, _dp, _dp, _dp, _dp]
+        for f in (L.oracle_grid, L.oracle_mask, L.oracle_energy, L.oracle_ground_state, L.oracle_propagate,
+                  L.oracle_adjoint):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -125,6 +131,23 @@ def propagate(psi0, E, dx, dt, a, Z=1.0, scheme=FULL_CN, mask_values=None, n_beg
                                   psi.view(np.float64).ctypes.data_as(_dp), _ptr(d), _ptr(acc)),
            "oracle_propagate")
     return psi, d, acc
+
+
+def adjoint(psi0, E, dx, dt, a, gd, ga, Z=1.0, mask_values=None):
+    """dL/dE_n for a loss with gradients gd = dL/dd_n, ga = dL/da_n through the FULL_CN forward map
+    (exact discrete adjoint; see oracle_adjoint)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+    gd = np.ascontiguousarray(gd, dtype=np.float64)
+    ga = np.ascontiguousarray(ga, dtype=np.float64)
+    if gd.size != E.size or ga.size != E.size:
+        raise ValueError("gd and ga need one entry per field sample")
+    gE = np.zeros(E.size)
+    m = None if mask_values is None else np.ascontiguousarray(mask_values, dtype=np.float64)
+    _check(lib().oracle_adjoint(psi0.size, dx, a, Z, dt, _ptr(m), _ptr(E), E.size - 1,
+                                psi0.view(np.float64).ctypes.data_as(_dp), _ptr(gd), _ptr(ga), _ptr(gE)),
+           "oracle_adjoint")
+    return gE
 
 
 def spectrum(acc, dt):

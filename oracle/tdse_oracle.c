@@ -334,3 +334,107 @@ int oracle_propagate(int N, double dx, double a, double Z, int scheme, double dt
     for (int k = 0; k < 3; ++k) { free(K[k]); free(M[k]); }
     return 0;
 }
+
+/* ---------------------------------------------------------------- discrete adjoint of FULL_CN */
+
+/* Gradient of a loss L(d, a) with respect to every field sample, through the FULL_CN forward map
+ * (the exact derivative of the discrete scheme, so it matches finite differences of the scheme).
+ * Inputs: the initial state psi0 (N complex), the field E[0..Nt], the mask (NULL = off), and the
+ * loss gradients gd[n] = dL/dd_n, ga[n] = dL/da_n for n = 0..Nt.  Output: gE[n] = dL/dE_n.
+ *
+ * With lambda^n = 2 dL/d conj(psi^n) (so that dL = Re sum conj(lambda) dpsi):
+ *   forward   A_n psi~^{n+1} = B_n psi^n,  psi^{n+1} = M psi~^{n+1},
+ *             A_n = 1 + i h H(Ebar_n), B_n = 1 - i h H(Ebar_n), h = dt/2, M = diag(m)
+ *   terminal  lambda^{Nt} = g^{Nt}
+ *   backward  mu = B_n^{-1} M lambda^{n+1}   (A_n^H = B_n because H is real symmetric)
+ *             lambda^n = A_n mu + g^n
+ *   local     g^n_j = 2 dx (gd_n x_j + ga_n (dV_j + E_n)) psi^n_j
+ *   field     dL/dEbar_n = h sum_j x_j Im(conj(mu_j) (psi^n_j + psi~^{n+1}_j)), split half to E_n and
+ *             half to E_{n+1} (Ebar_n = (E_n + E_{n+1})/2); plus dL/dE_n += ga_n dx sum_j |psi^n_j|^2. */
+int oracle_adjoint(int N, double dx, double a, double Z, double dt, const double* mask, const double* E, long Nt,
+                   const double* psi0_ri, const double* gd, const double* ga, double* gE)
+{
+    if (N < 3 || !(dx > 0.0) || !(a > 0.0) || Nt < 0 || !E || !psi0_ri || !gd || !ga || !gE) return -1;
+    const double h = 0.5 * dt;
+    const double complex c = I * h;
+    double* x = malloc(sizeof(double) * N);
+    double* V = malloc(sizeof(double) * N);
+    double* dV = malloc(sizeof(double) * N);
+    double* K[3]; double* M[3];
+    for (int k = 0; k < 3; ++k) { K[k] = malloc(sizeof(double) * N); M[k] = malloc(sizeof(double) * N); }
+    double complex* psi = malloc(sizeof(double complex) * (size_t)N * (Nt + 1));     /* psi^n, n = 0..Nt */
+    double complex* pt = malloc(sizeof(double complex) * (size_t)N * (Nt + 1));      /* psi~^n, n = 1..Nt */
+    double complex* lo = malloc(sizeof(double complex) * N);
+    double complex* di = malloc(sizeof(double complex) * N);
+    double complex* up = malloc(sizeof(double complex) * N);
+    double complex* blo = malloc(sizeof(double complex) * N);
+    double complex* bdi = malloc(sizeof(double complex) * N);
+    double complex* bup = malloc(sizeof(double complex) * N);
+    double complex* r = malloc(sizeof(double complex) * N);
+    double complex* lam = malloc(sizeof(double complex) * N);
+    double complex* mu = malloc(sizeof(double complex) * N);
+    double complex* work = malloc(sizeof(double complex) * 2 * N);
+    int ok = x && V && dV && psi && pt && lo && di && up && blo && bdi && bup && r && lam && mu && work;
+    for (int k = 0; k < 3; ++k) ok = ok && K[k] && M[k];
+    if (!ok) {
+        free(x); free(V); free(dV); free(psi); free(pt); free(lo); free(di); free(up); free(blo); free(bdi);
+        free(bup); free(r); free(lam); free(mu); free(work);
+        for (int k = 0; k < 3; ++k) { free(K[k]); free(M[k]); }
+        return -2;
+    }
+    oracle_grid(N, dx, a, Z, x, V, dV);
+    assemble(N, dx, V, ORACLE_FULL_CN, K[0], K[1], K[2], M[0], M[1], M[2]);
+    memcpy(psi, psi0_ri, sizeof(double complex) * N);
+    /* forward pass, keeping every state */
+    for (long n = 0; n < Nt; ++n) {
+        double Ebar = 0.5 * (E[n] + E[n + 1]);
+        for (int j = 0; j < N; ++j) {
+            double kd = K[1][j] + x[j] * Ebar;
+            lo[j] = c * K[0][j];   di[j] = 1.0 + c * kd;  up[j] = c * K[2][j];
+            blo[j] = -c * K[0][j]; bdi[j] = 1.0 - c * kd; bup[j] = -c * K[2][j];
+        }
+        tri_apply(N, blo, bdi, bup, psi + (size_t)n * N, r);
+        tri_solve(N, lo, di, up, r, pt + (size_t)(n + 1) * N, work);
+        for (int j = 0; j < N; ++j)
+            psi[(size_t)(n + 1) * N + j] = (mask ? mask[j] : 1.0) * pt[(size_t)(n + 1) * N + j];
+    }
+    for (long n = 0; n <= Nt; ++n) gE[n] = 0.0;
+    /* terminal adjoint and the direct field term of a_Nt */
+    {
+        const double complex* p = psi + (size_t)Nt * N;
+        double nrm = 0.0;
+        for (int j = 0; j < N; ++j) {
+            lam[j] = 2.0 * dx * (gd[Nt] * x[j] + ga[Nt] * (dV[j] + E[Nt])) * p[j];
+            nrm += creal(p[j]) * creal(p[j]) + cimag(p[j]) * cimag(p[j]);
+        }
+        gE[Nt] += ga[Nt] * dx * nrm;
+    }
+    for (long n = Nt - 1; n >= 0; --n) {
+        double Ebar = 0.5 * (E[n] + E[n + 1]);
+        for (int j = 0; j < N; ++j) {
+            double kd = K[1][j] + x[j] * Ebar;
+            lo[j] = c * K[0][j];   di[j] = 1.0 + c * kd;  up[j] = c * K[2][j];
+            blo[j] = -c * K[0][j]; bdi[j] = 1.0 - c * kd; bup[j] = -c * K[2][j];
+        }
+        for (int j = 0; j < N; ++j) r[j] = (mask ? mask[j] : 1.0) * lam[j];
+        tri_solve(N, blo, bdi, bup, r, mu, work);               /* mu = B_n^{-1} M lambda^{n+1} */
+        const double complex* p = psi + (size_t)n * N;
+        const double complex* q = pt + (size_t)(n + 1) * N;
+        double gbar = 0.0;
+        for (int j = 0; j < N; ++j) gbar += x[j] * cimag(conj(mu[j]) * (p[j] + q[j]));
+        gbar *= h;
+        gE[n] += 0.5 * gbar;
+        gE[n + 1] += 0.5 * gbar;
+        tri_apply(N, lo, di, up, mu, lam);                      /* lambda^n = A_n mu + g^n */
+        double nrm = 0.0;
+        for (int j = 0; j < N; ++j) {
+            lam[j] += 2.0 * dx * (gd[n] * x[j] + ga[n] * (dV[j] + E[n])) * p[j];
+            nrm += creal(p[j]) * creal(p[j]) + cimag(p[j]) * cimag(p[j]);
+        }
+        gE[n] += ga[n] * dx * nrm;
+    }
+    free(x); free(V); free(dV); free(psi); free(pt); free(lo); free(di); free(up); free(blo); free(bdi);
+    free(bup); free(r); free(lam); free(mu); free(work);
+    for (int k = 0; k < 3; ++k) { free(K[k]); free(M[k]); }
+    return 0;
+}

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -24,6 +25,18 @@ tdse_status fail(tdse_status st, const std::string& msg)
     g_last_error = msg;
     return st;
 }
+
+}  // namespace
+
+namespace tdse {
+const char* set_error_message(const char* msg)
+{
+    g_last_error = msg ? msg : "";
+    return g_last_error.c_str();
+}
+}  // namespace tdse
+
+namespace {
 
 tdse_status cuda_fail(cudaError_t e, const char* what)
 {
@@ -76,9 +89,11 @@ struct tdse_batch {
     std::vector<int64_t> slot_of_inst;
     std::vector<GroupDesc> groups;
     std::vector<int> class_P, class_K;
-    std::vector<int64_t> class_group_begin, class_group_end;
     int64_t n_slots = 0;
-    int segments_override = 0;
+    // launch configuration of the persistent propagation kernel
+    int warps_override = 0, ctas_per_sm_override = 0, slice_override = 0, max_ctas_override = 0;
+    int warps = 8, ctas = 0, rows = 0, slice = 16;
+    int sm_count = 0;
     bool initialized = false;
     // device memory
     ClassDesc* d_cls = nullptr;
@@ -87,14 +102,18 @@ struct tdse_batch {
     int64_t* d_slot_row = nullptr;
     int64_t* d_slot_nt = nullptr;
     int64_t* d_slot_valid = nullptr;
-    double2* d_psi = nullptr;
-    double2* d_scratch = nullptr;
+    void* d_psi = nullptr;       // double2 (FP64) or float2 (MIXED) elements
+    void* d_scratch = nullptr;
+    int* d_busy = nullptr;
+    int* d_progress = nullptr;
     int* d_status = nullptr;
     double* d_gs_work = nullptr;
     int64_t* d_gs_off = nullptr;
     double* d_gs_energy = nullptr;
     int64_t* d_gs_iters = nullptr;
     int64_t psi_elems = 0, scratch_elems = 0;
+    int mixed() const { return precision == TDSE_MIXED ? 1 : 0; }
+    size_t cx_bytes() const { return precision == TDSE_MIXED ? sizeof(float2) : sizeof(double2); }
 };
 
 namespace {
@@ -109,6 +128,8 @@ void free_device(tdse_batch* b)
     cudaFree(b->d_slot_valid);
     cudaFree(b->d_psi);
     cudaFree(b->d_scratch);
+    cudaFree(b->d_busy);
+    cudaFree(b->d_progress);
     cudaFree(b->d_status);
     cudaFree(b->d_gs_work);
     cudaFree(b->d_gs_off);
@@ -119,6 +140,7 @@ void free_device(tdse_batch* b)
     b->d_tab = nullptr;
     b->d_slot_row = b->d_slot_nt = b->d_slot_valid = nullptr;
     b->d_psi = b->d_scratch = nullptr;
+    b->d_busy = b->d_progress = nullptr;
     b->d_status = nullptr;
     b->d_gs_work = nullptr;
     b->d_gs_off = nullptr;
@@ -126,61 +148,90 @@ void free_device(tdse_batch* b)
     b->d_gs_iters = nullptr;
 }
 
-// Halo length K such that beta^K < 1e-18 (the truncated sweeps then agree with the exact Thomas
-// solve below double rounding); 0 when beta is too close to 1 for truncation to pay off.
-int halo_for_beta(double beta)
+// NUMEROV_SPLIT: LU factors of the time-independent A = M2 + i h (-Delta2/2 + M2 V), h = dt/2
+// (Sec. 4.2, Eq. "CN - step 2"), M2 = tridiag(1, 10, 1)/12, (M2 V)_{jk} = (M2)_{jk} V_k:
+//   A_{j,j-1} = 1/12 + i h (-1/(2dx^2) + V_{j-1}/12), A_{jj} = 10/12 + i h (1/dx^2 + 10 V_j/12),
+//   A_{j,j+1} = 1/12 + i h (-1/(2dx^2) + V_{j+1}/12);
+// Thomas from j = 0: pivot_j = A_jj - A_{j,j-1} C_{j-1}, W_j = 1/pivot_j, L_j = A_{j,j-1} W_j,
+// C_j = A_{j,j+1} W_j.  Writes (W_j/12, L_j, C_j) as double pairs and float pairs into the host
+// images of the nw/nl/nc/nf tables and returns max(|L|, |C|).
+double numerov_factors(const ClassDesc& C, double dt, std::vector<double>& nw, std::vector<double>& nl,
+                       std::vector<double>& nc, std::vector<float>& nf)
 {
-    const double b = std::fabs(beta);
-    if (b >= 0.85) return 0;
-    if (b < 1e-3) return 8;
-    int K = (int)std::ceil(std::log(1e-18) / std::log(b));
-    return std::max(K, 8);
-}
-
-// Segments per instance: enough warps to fill the GPU (about 8 per SM on 152 SMs) while keeping
-// every segment at least 4 halos long.
-int plan_segments(int N, int K, int64_t total_groups, int override_P)
-{
-    if (K == 0) return 1;
-    int max_P = std::max(1, std::min(kMaxSegments, N / std::max(4 * K, 16)));
-    int P;
-    if (override_P > 0) {
-        P = override_P;
-    } else {
-        const int64_t want_warps = 152 * 8;
-        P = (int)std::min<int64_t>(kMaxSegments, (want_warps + total_groups - 1) / std::max<int64_t>(total_groups, 1));
+    using cd = std::complex<double>;
+    const int N = C.N;
+    const double h = 0.5 * dt, inv = 1.0 / (C.dx * C.dx);
+    std::vector<double> V(N);
+    for (int j = 0; j < N; ++j) {
+        const double x = (j - 0.5 * (N - 1)) * C.dx;
+        V[j] = -C.Z / std::sqrt(x * x + C.a * C.a);
     }
-    return std::max(1, std::min(P, max_P));
+    nw.assign(2 * (size_t)N, 0.0);
+    nl.assign(2 * (size_t)N, 0.0);
+    nc.assign(2 * (size_t)N, 0.0);
+    nf.assign(6 * (size_t)N, 0.0f);
+    double rho = 0.0;
+    cd cprev(0.0, 0.0);
+    for (int j = 0; j < N; ++j) {
+        const cd lo = j > 0 ? cd(1.0 / 12.0, h * (-0.5 * inv + V[j - 1] / 12.0)) : cd(0.0, 0.0);
+        const cd di(10.0 / 12.0, h * (inv + (10.0 / 12.0) * V[j]));
+        const cd up = j < N - 1 ? cd(1.0 / 12.0, h * (-0.5 * inv + V[j + 1] / 12.0)) : cd(0.0, 0.0);
+        const cd piv = di - lo * cprev;
+        const cd W = 1.0 / piv;
+        const cd L = lo * W;
+        const cd Cj = up * W;
+        const cd W12 = W / 12.0;
+        nw[2 * j] = W12.real();
+        nw[2 * j + 1] = W12.imag();
+        nl[2 * j] = L.real();
+        nl[2 * j + 1] = L.imag();
+        nc[2 * j] = Cj.real();
+        nc[2 * j + 1] = Cj.imag();
+        nf[6 * j + 0] = (float)W12.real();
+        nf[6 * j + 1] = (float)W12.imag();
+        nf[6 * j + 2] = (float)L.real();
+        nf[6 * j + 3] = (float)L.imag();
+        nf[6 * j + 4] = (float)Cj.real();
+        nf[6 * j + 5] = (float)Cj.imag();
+        rho = std::max(rho, std::max(std::abs(L), std::abs(Cj)));
+        cprev = Cj;
+    }
+    return rho;
 }
 
-// (Re)compute the per-class plan, group descriptors and scratch size, and (re)allocate scratch.
+// (Re)compute the launch configuration, the group descriptors and the scratch, and (re)allocate.
 tdse_status build_plan(tdse_batch* b)
 {
     const int n_cls = (int)b->classes.size();
+    b->warps = b->warps_override > 0 ? b->warps_override : 8;
+    b->slice = b->slice_override > 0 ? b->slice_override : 16;
     b->class_P.assign(n_cls, 1);
     b->class_K.assign(n_cls, 0);
-    const int64_t total_groups = (int64_t)b->groups.size();
     for (int c = 0; c < n_cls; ++c) {
         const ClassDesc& C = b->classes[c];
-        int K = halo_for_beta(C.beta);
-        int P = plan_segments(C.N, K, total_groups, b->segments_override);
+        int K = halo_for_beta(b->scheme == TDSE_NUMEROV_SPLIT ? C.rho : C.beta);
+        const int P = class_segments(C.N, K, b->warps);
         if (P == 1) K = 0;
         b->class_P[c] = P;
         b->class_K[c] = K;
     }
-    int64_t sc = 0;
+    int rows = 1;
     for (auto& G : b->groups) {
         const int P = b->class_P[G.cls], K = b->class_K[G.cls];
         G.P = P;
         G.K = K;
         G.m = (G.N + P - 1) / P;
-        G.rows = std::min(G.N, G.m + 2 * K);
-        G.scratch_off = sc;
-        sc += (int64_t)P * G.rows * 2 * kLanes;
+        rows = std::max(rows, std::min(G.N, G.m + 2 * K));
     }
+    b->rows = rows;
+    const int per_sm_max = propagate_max_ctas_per_sm(b->mixed(), b->warps);
+    const int per_sm = b->ctas_per_sm_override > 0 ? std::min(b->ctas_per_sm_override, per_sm_max) : 1;
+    b->ctas = (int)std::min<int64_t>((int64_t)b->groups.size(), (int64_t)b->sm_count * per_sm);
+    if (b->max_ctas_override > 0) b->ctas = std::min(b->ctas, b->max_ctas_override);
+    const int64_t sc = (int64_t)b->ctas * b->warps * rows * 2 * kLanes;
     cudaFree(b->d_scratch);
     b->d_scratch = nullptr;
-    TDSE_CUDA(dev_alloc(&b->d_scratch, (size_t)sc), "cudaMalloc(scratch)");
+    TDSE_CUDA(cudaMalloc(&b->d_scratch, (size_t)std::max<int64_t>(sc, 1) * b->cx_bytes()), "cudaMalloc(scratch)");
     b->scratch_elems = sc;
     TDSE_CUDA(cudaMemcpy(b->d_groups, b->groups.data(), sizeof(GroupDesc) * b->groups.size(), cudaMemcpyHostToDevice),
               "cudaMemcpy(groups)");
@@ -204,8 +255,8 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     if (!inst_host || !n_steps_host || !row_offsets_host) return fail(TDSE_ERR_ARG, "tdse_batch_create: NULL array");
     if (n_inst < 1 || n_inst > (int64_t(1) << 31)) return fail(TDSE_ERR_ARG, "tdse_batch_create: n_inst out of range");
     if (!is_finite(dt) || dt == 0.0) return fail(TDSE_ERR_ARG, "tdse_batch_create: dt must be finite and non-zero");
-    if (precision != TDSE_FP64) return fail(TDSE_ERR_ARG, "tdse_batch_create: only TDSE_FP64 is available in this build");
-    if (scheme != TDSE_FULL_CN) return fail(TDSE_ERR_ARG, "tdse_batch_create: only TDSE_FULL_CN is available in this build");
+    if (precision != TDSE_FP64 && precision != TDSE_MIXED) return fail(TDSE_ERR_ARG, "tdse_batch_create: unknown precision");
+    if (scheme != TDSE_FULL_CN && scheme != TDSE_NUMEROV_SPLIT) return fail(TDSE_ERR_ARG, "tdse_batch_create: unknown scheme");
     if (absorber && (!is_finite(absorber->width) || !is_finite(absorber->exponent) || absorber->exponent < 0.0))
         return fail(TDSE_ERR_ARG, "tdse_batch_create: bad absorber");
     if (row_offsets_host[0] < 0) return fail(TDSE_ERR_ARG, "tdse_batch_create: row_offsets[0] < 0");
@@ -297,12 +348,9 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     });
     b->slot_of_inst.assign(n_inst, -1);
     std::vector<int64_t> slot_row, slot_nt, slot_valid;
-    b->class_group_begin.assign(n_cls, 0);
-    b->class_group_end.assign(n_cls, 0);
     int64_t psi_elems = 0;
     for (int64_t k = 0; k < n_inst;) {
         const int c = b->inst_class[order[k]];
-        b->class_group_begin[c] = (int64_t)b->groups.size();
         while (k < n_inst && b->inst_class[order[k]] == c) {
             GroupDesc G{};
             G.cls = c;
@@ -327,7 +375,6 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
             }
             b->groups.push_back(G);
         }
-        b->class_group_end[c] = (int64_t)b->groups.size();
     }
     b->n_slots = (int64_t)slot_row.size();
     b->psi_elems = psi_elems;
@@ -346,8 +393,13 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     if ((e = dev_alloc(&b->d_slot_row, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
     if ((e = dev_alloc(&b->d_slot_nt, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
     if ((e = dev_alloc(&b->d_slot_valid, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
-    if ((e = dev_alloc(&b->d_psi, (size_t)psi_elems)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(psi)"));
+    if ((e = cudaMalloc(&b->d_psi, (size_t)std::max<int64_t>(psi_elems, 1) * b->cx_bytes())) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMalloc(psi)"));
     if ((e = dev_alloc(&b->d_status, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(status)"));
+    if ((e = dev_alloc(&b->d_busy, b->groups.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(sched)"));
+    if ((e = dev_alloc(&b->d_progress, b->groups.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(sched)"));
+    if ((e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
     int64_t gs_total = 0;
     std::vector<int64_t> gs_off(n_cls);
     for (int c = 0; c < n_cls; ++c) {
@@ -364,12 +416,26 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
         (e = cudaMemcpy(b->d_slot_valid, slot_valid.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->d_gs_off, gs_off.data(), sizeof(int64_t) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(b->d_status, 0, sizeof(int) * b->n_slots)) != cudaSuccess ||
-        (e = cudaMemset(b->d_psi, 0, sizeof(double2) * (size_t)std::max<int64_t>(psi_elems, 1))) != cudaSuccess)
+        (e = cudaMemset(b->d_psi, 0, b->cx_bytes() * (size_t)std::max<int64_t>(psi_elems, 1))) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemcpy(setup)"));
-    if ((st = build_plan(b)) != TDSE_OK) return bail(st);
     if ((e = launch_build_tables(b->d_cls, n_cls, max_N, dt, b->mask_width, b->mask_exp, b->mask_on, b->d_tab, 0)) != cudaSuccess)
         return bail(cuda_fail(e, "build_tables launch"));
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "build_tables"));
+    if (scheme == TDSE_NUMEROV_SPLIT) {
+        std::vector<double> nw, nl, nc;
+        std::vector<float> nf;
+        for (auto& C : b->classes) {
+            C.rho = numerov_factors(C, dt, nw, nl, nc, nf);
+            if ((e = cudaMemcpy(b->d_tab + tab_nw(C), nw.data(), sizeof(double) * nw.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(b->d_tab + tab_nl(C), nl.data(), sizeof(double) * nl.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(b->d_tab + tab_nc(C), nc.data(), sizeof(double) * nc.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(b->d_tab + tab_nf(C), nf.data(), sizeof(float) * nf.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return bail(cuda_fail(e, "cudaMemcpy(numerov tables)"));
+        }
+        if ((e = cudaMemcpy(b->d_cls, b->classes.data(), sizeof(ClassDesc) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMemcpy(classes)"));
+    }
+    if ((st = build_plan(b)) != TDSE_OK) return bail(st);
     *out = b;
     return TDSE_OK;
 }
@@ -389,19 +455,29 @@ tdse_status tdse_plan(const tdse_batch* b, tdse_plan_info* info)
     info->n_groups = (int64_t)b->groups.size();
     info->segments = b->class_P.empty() ? 0 : *std::max_element(b->class_P.begin(), b->class_P.end());
     info->halo = b->class_K.empty() ? 0 : *std::max_element(b->class_K.begin(), b->class_K.end());
-    info->scratch_bytes = b->scratch_elems * (int64_t)sizeof(double2);
-    info->psi_bytes = b->psi_elems * (int64_t)sizeof(double2);
+    info->warps_per_cta = b->warps;
+    info->ctas = b->ctas;
+    info->slice_steps = b->slice;
+    info->scratch_bytes = b->scratch_elems * (int64_t)b->cx_bytes();
+    info->psi_bytes = b->psi_elems * (int64_t)b->cx_bytes();
     return TDSE_OK;
 }
 
-tdse_status tdse_set_segments(tdse_batch* b, int32_t segments)
+tdse_status tdse_set_launch(tdse_batch* b, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
+                            int32_t max_ctas)
 {
-    if (!b) return fail(TDSE_ERR_ARG, "tdse_set_segments: NULL batch");
-    if (segments < 0 || segments > kMaxSegments) return fail(TDSE_ERR_ARG, "tdse_set_segments: out of [0, 16]");
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_set_launch: NULL batch");
+    if (warps_per_cta < 0 || warps_per_cta > kMaxSegments) return fail(TDSE_ERR_ARG, "tdse_set_launch: warps_per_cta out of [0, 16]");
+    if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(TDSE_ERR_ARG, "tdse_set_launch: ctas_per_sm out of [0, 32]");
+    if (slice_steps < 0) return fail(TDSE_ERR_ARG, "tdse_set_launch: slice_steps < 0");
+    if (max_ctas < 0) return fail(TDSE_ERR_ARG, "tdse_set_launch: max_ctas < 0");
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
-    TDSE_CUDA(cudaDeviceSynchronize(), "tdse_set_segments: synchronize");
-    b->segments_override = segments;
+    TDSE_CUDA(cudaDeviceSynchronize(), "tdse_set_launch: synchronize");
+    b->warps_override = warps_per_cta;
+    b->ctas_per_sm_override = ctas_per_sm;
+    b->slice_override = slice_steps;
+    b->max_ctas_override = max_ctas;
     return build_plan(b);
 }
 
@@ -419,8 +495,8 @@ tdse_status tdse_ground_state(tdse_batch* b, double dtau, int64_t max_iter, doub
     TDSE_CUDA(launch_ground_state(b->d_cls, n_cls, (int)b->scheme, dtau, max_iter, tol, b->d_gs_work, b->d_gs_off,
                                   b->d_gs_energy, b->d_gs_iters, st),
               "ground_state launch");
-    TDSE_CUDA(launch_broadcast_psi(b->d_groups, (int64_t)b->groups.size(), b->d_gs_work, b->d_gs_off, b->d_slot_valid,
-                                   b->d_psi, st),
+    TDSE_CUDA(launch_broadcast_psi(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->d_gs_work, b->d_gs_off,
+                                   b->d_slot_valid, b->d_psi, st),
               "broadcast launch");
     b->initialized = true;
     if (energies_host || iters_host) {
@@ -458,13 +534,18 @@ tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, do
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t st = (cudaStream_t)stream;
-    for (size_t c = 0; c < b->classes.size(); ++c) {
-        const int64_t g0 = b->class_group_begin[c], g1 = b->class_group_end[c];
-        TDSE_CUDA(launch_propagate_fp64(b->d_groups, g0, g1 - g0, b->class_P[c], b->d_cls, b->d_tab, b->d_slot_row,
-                                        b->d_slot_nt, b->d_psi, b->d_scratch, E_dev, d_dev, a_dev, sample_base,
-                                        step_begin, step_end, b->mask_on, b->d_status, st),
+    if (b->scheme == TDSE_NUMEROV_SPLIT)
+        TDSE_CUDA(launch_propagate_numerov(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas,
+                                           b->d_cls, b->d_tab, b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_scratch,
+                                           b->rows, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, b->slice,
+                                           b->mask_on, b->dt, b->d_busy, b->d_progress, b->d_status, st),
                   "propagate launch");
-    }
+    else
+        TDSE_CUDA(launch_propagate_full_cn(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas,
+                                           b->d_cls, b->d_tab, b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_scratch,
+                                           b->rows, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, b->slice,
+                                           b->mask_on, b->d_busy, b->d_progress, b->d_status, st),
+                  "propagate launch");
     return TDSE_OK;
 }
 
@@ -488,7 +569,7 @@ tdse_status tdse_get_psi(tdse_batch* b, int64_t inst, double* psi_dev, void* str
     if (s != TDSE_OK) return s;
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
-    TDSE_CUDA(launch_get_psi(b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "get_psi launch");
+    TDSE_CUDA(launch_get_psi(b->mixed(), b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "get_psi launch");
     return TDSE_OK;
 }
 
@@ -501,7 +582,7 @@ tdse_status tdse_set_psi(tdse_batch* b, int64_t inst, const double* psi_dev, voi
     if (s != TDSE_OK) return s;
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
-    TDSE_CUDA(launch_set_psi(b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "set_psi launch");
+    TDSE_CUDA(launch_set_psi(b->mixed(), b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "set_psi launch");
     b->initialized = true;
     return TDSE_OK;
 }
@@ -520,7 +601,7 @@ tdse_status tdse_check(tdse_batch* b, int64_t* first_bad, void* stream)
     for (int64_t i = 0; i < b->n_inst && bad < 0; ++i)
         if (flags[b->slot_of_inst[i]]) bad = i;
     if (first_bad) *first_bad = bad;
-    if (bad >= 0) return fail(TDSE_ERR_NONFINITE, "instance " + std::to_string(bad) + ": norm non-finite or above 1 + 1e-6");
+    if (bad >= 0) return fail(TDSE_ERR_NONFINITE, "instance " + std::to_string(bad) + ": norm non-finite or above its rounding allowance");
     return TDSE_OK;
 }
 

@@ -1,6 +1,8 @@
 // Internal declarations shared by the C-ABI layer (tdse_api.cu) and the kernels (tdse_kernels.cu).
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -9,27 +11,30 @@ namespace tdse {
 constexpr int kLanes = 32;          // instances per group: one per lane of a warp
 constexpr int kMaxSegments = 16;    // warps per CTA at most (512 threads)
 
-// Per-class tables (one class = one distinct (N, dx, a, Z)), all length N:
-//   ab[j]  = (S0_j, Xh_j)  with S0_j = dt/2 (1/dx^2 + V_j), Xh_j = dt/2 x_j   (FULL_CN diagonal)
-//   xv[j]  = (x_j, dV_j)                                                   (observables)
-//   mk[j]  = m_j                                                           (edge mask)
+// Per-class tables (one class = one distinct (N, dx, a, Z)), all of length N, in doubles:
+//   ab[j]  = (S0_j/beta, Xh_j/beta), S0_j = dt/2 (1/dx^2 + V_j), Xh_j = dt/2 x_j  (FULL_CN diagonal)
+//   xv[j]  = (x_j, dV_j)                                                  (observables)
+//   mk[j]  = m_j                                                          (edge mask)
+//   nw[j], nl[j], nc[j]: NUMEROV_SPLIT factors of A = M2 + i dt/2 (-Delta2/2 + M2 V) (complex):
+//            W_j/12 = 1/(12 pivot_j), L_j = A_{j,j-1}/pivot_j, C_j = A_{j,j+1}/pivot_j
+//   nf[3j..3j+2] = the same three factors rounded to float2 (MIXED)
 struct ClassDesc {
     int64_t tab_off;      // offset (in doubles) of the class block in the table buffer
     int32_t N;
     int32_t jm_lo, jm_hi; // m_j == 1 exactly for jm_lo <= j <= jm_hi
     double dx, a, Z;
     double beta;          // dt / (4 dx^2): magnitude of the off-diagonal of 1 + i dt/2 H
+    double rho;           // NUMEROV_SPLIT: max_j max(|L_j|, |C_j|), the decay rate of its sweeps
 };
 
-// One CTA of the propagation kernel = one group of 32 instances of one class.
+// A group = 32 instances of one class, one per lane.  The propagation kernel processes a group
+// with one CTA at a time (P warps, the group uses the first P_g of them).
 struct GroupDesc {
     int64_t psi_off;      // complex-element offset of the group's wavefunctions, layout [N][32]
-    int64_t scratch_off;  // complex-element offset of the group's scratch, layout [P][rows][2][32]
     int64_t slot0;        // first slot (slot = group * 32 + lane)
     int64_t nt_max;       // largest Nt over the group's real instances
     int32_t cls;          // class index
-    int32_t N, P, K, m;   // grid size, segments (warps), halo, segment length
-    int32_t rows;         // scratch rows per warp = m + 2K (clamped to N)
+    int32_t N, P, K, m;   // grid size, segments used (<= warps per CTA), halo, segment length
     int32_t pad;
 };
 
@@ -37,7 +42,37 @@ struct GroupDesc {
 __host__ __device__ inline int64_t tab_ab(const ClassDesc& c) { return c.tab_off; }
 __host__ __device__ inline int64_t tab_xv(const ClassDesc& c) { return c.tab_off + 2 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_mk(const ClassDesc& c) { return c.tab_off + 4 * (int64_t)c.N; }
-inline int64_t tab_doubles(int N) { return 5 * (int64_t)N; }
+__host__ __device__ inline int64_t tab_nw(const ClassDesc& c) { return c.tab_off + 5 * (int64_t)c.N; }
+__host__ __device__ inline int64_t tab_nl(const ClassDesc& c) { return c.tab_off + 7 * (int64_t)c.N; }
+__host__ __device__ inline int64_t tab_nc(const ClassDesc& c) { return c.tab_off + 9 * (int64_t)c.N; }
+__host__ __device__ inline int64_t tab_nf(const ClassDesc& c) { return c.tab_off + 11 * (int64_t)c.N; }
+inline int64_t tab_doubles(int N) { return 14 * (int64_t)N; }
+
+// ---- host-side planning rules shared by the allocating and the static entry points ----
+
+// Halo length K such that beta^K < 1e-18: the truncated sweeps then agree with the exact Thomas
+// solve below double rounding (|gamma| <= |beta| per point, see tdse_propagate.cu); 0 when beta is
+// too close to 1 for truncation to pay off.
+inline int halo_for_beta(double beta)
+{
+    const double b = std::fabs(beta);
+    if (b >= 0.85) return 0;
+    if (b < 1e-3) return 8;
+    const int K = (int)std::ceil(std::log(1e-18) / std::log(b));
+    return std::max(K, 8);
+}
+
+// Segments of a class: at most the CTA's warps, and every segment at least four halos long
+// (otherwise the halo work dominates); one exact segment when no halo applies.
+inline int class_segments(int N, int K, int warps)
+{
+    if (K == 0) return 1;
+    const int max_P = std::max(1, N / std::max(4 * K, 16));
+    return std::max(1, std::min(warps, max_P));
+}
+
+// Stores the calling thread's last-error message (tdse_api.cu).
+const char* set_error_message(const char* msg);
 
 // ---- kernel launchers (tdse_kernels.cu); all return cudaGetLastError() after the launch ----
 
@@ -51,18 +86,32 @@ cudaError_t launch_ground_state(const ClassDesc* d_cls, int n_cls, int scheme, d
                                 int64_t* d_iters, cudaStream_t st);
 
 // Copy each class's real ground state (first N doubles of its work block) into every slot of the class.
-cudaError_t launch_broadcast_psi(const GroupDesc* d_groups, int64_t n_groups, const double* d_work,
-                                 const int64_t* d_work_off, const int64_t* d_slot_valid, double2* d_psi,
+cudaError_t launch_broadcast_psi(int mixed, const GroupDesc* d_groups, int64_t n_groups, const double* d_work,
+                                 const int64_t* d_work_off, const int64_t* d_slot_valid, void* d_psi,
                                  cudaStream_t st);
 
-cudaError_t launch_propagate_fp64(const GroupDesc* d_groups, int64_t g_begin, int64_t n_groups, int P,
-                                  const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
-                                  const int64_t* d_slot_nt, double2* d_psi, double2* d_scratch, const double* E,
-                                  double* d_out, double* a_out, int64_t sample_base, int64_t step_begin,
-                                  int64_t step_end, int mask_on, int* d_status, cudaStream_t st);
+// Persistent FULL_CN propagation (tdse_propagate.cu): `ctas` CTAs of P warps pick groups
+// dynamically, `slice` steps at a time.  mixed = 0: psi and scratch are double2; mixed = 1:
+// float2.  Scratch holds ctas * P * rows rows of 2 * 32 complex values.
+cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
+                                     const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
+                                     const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
+                                     const double* E, double* d_out, double* a_out, int64_t sample_base,
+                                     int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
+                                     int* d_progress, int* d_status, cudaStream_t st);
+int propagate_max_ctas_per_sm(int mixed, int P);
 
-cudaError_t launch_get_psi(const double2* d_psi, int64_t psi_off, int N, int lane, double* out, cudaStream_t st);
-cudaError_t launch_set_psi(double2* d_psi, int64_t psi_off, int N, int lane, const double* in, cudaStream_t st);
+// Persistent NUMEROV_SPLIT propagation (same scheduler, scratch and layouts; tables nw/nl/nc/nf).
+cudaError_t launch_propagate_numerov(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
+                                     const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
+                                     const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
+                                     const double* E, double* d_out, double* a_out, int64_t sample_base,
+                                     int64_t step_begin, int64_t step_end, int slice, int mask_on, double dt,
+                                     int* d_busy, int* d_progress, int* d_status, cudaStream_t st);
+
+cudaError_t launch_get_psi(int mixed, const void* d_psi, int64_t psi_off, int N, int lane, double* out,
+                           cudaStream_t st);
+cudaError_t launch_set_psi(int mixed, void* d_psi, int64_t psi_off, int N, int lane, const double* in, cudaStream_t st);
 
 cudaError_t launch_spectrum(const double* a, const int64_t* d_offsets, int64_t n_rows, double dt, int64_t k_begin,
                             int64_t k_end, double* S, cudaStream_t st);

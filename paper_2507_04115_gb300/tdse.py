@@ -20,7 +20,7 @@ _lib = None
 
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
-           "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_segments", "tdse_last_error")
+           "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -34,6 +34,7 @@ class tdse_absorber(ctypes.Structure):
 
 class tdse_plan_info(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int64), ("segments", ctypes.c_int32), ("halo", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32), ("ctas", ctypes.c_int32), ("slice_steps", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64), ("psi_bytes", ctypes.c_int64)]
 
 
@@ -67,7 +68,7 @@ def load(path: str | None = None):
     L.tdse_check.argtypes = [_vp, _i64p, _vp]
     L.tdse_spectrum.argtypes = [_vp, _i64p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _vp, _vp]
     L.tdse_plan.argtypes = [_vp, ctypes.POINTER(tdse_plan_info)]
-    L.tdse_set_segments.argtypes = [_vp, ctypes.c_int32]
+    L.tdse_set_launch.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -213,10 +214,13 @@ class Batch:
         info = tdse_plan_info()
         _check(load().tdse_plan(self._h, ctypes.byref(info)))
         return dict(n_groups=info.n_groups, segments=info.segments, halo=info.halo,
+                    warps_per_cta=info.warps_per_cta, ctas=info.ctas, slice_steps=info.slice_steps,
                     scratch_bytes=info.scratch_bytes, psi_bytes=info.psi_bytes)
 
-    def set_segments(self, segments):
-        _check(load().tdse_set_segments(self._h, int(segments)))
+    def set_launch(self, warps_per_cta=0, ctas_per_sm=0, slice_steps=0, max_ctas=0):
+        """Override the persistent grid (see tdse_set_launch); 0 keeps a default."""
+        _check(load().tdse_set_launch(self._h, int(warps_per_cta), int(ctas_per_sm), int(slice_steps),
+                                      int(max_ctas)))
 
 
 def spectrum(a, offsets, dt, k_begin, k_end, out=None, stream=None):
@@ -229,3 +233,4 @@ def spectrum(a, offsets, dt, k_begin, k_end, out=None, stream=None):
     _check(load().tdse_spectrum(_dev_ptr(a, "a"), offs.ctypes.data_as(_i64p), n_rows, float(dt), int(k_begin),
                                 int(k_end), _dev_ptr(out, "S"), _stream_ptr(stream)))
     return out
+

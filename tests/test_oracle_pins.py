@@ -293,3 +293,36 @@ def test_spectrum_against_direct_sum(oracle_mod):
     St = oracle_mod.spectrum(tone, dt)
     assert abs(St[k0] - (L / 2) ** 2 * dt * dt) < 1e-10
     assert np.max(np.delete(St, [k0, L - k0])) < 1e-20
+
+
+# ---------------------------------------------------------------- discrete adjoint
+
+def test_adjoint_matches_central_differences(oracle_mod):
+    """dL/dE of a loss L = sum gd_n d_n + ga_n a_n (random weights) against central finite
+    differences of the forward oracle on several field samples, mask on."""
+    rng = np.random.default_rng(7)
+    N, dx, dt, a = 300, 0.2, 0.05, 1.19
+    nt = 240
+    psi0, _, _ = oracle_mod.ground_state(N, dx, a, tol=1e-13)
+    E = _sin2_pulse(nt, dt, 0.07, 0.057, 1) + 0.01 * rng.standard_normal(nt + 1)
+    m = oracle_mod.mask(N, dx, 15.0, 0.125)
+    gd = rng.standard_normal(nt + 1)
+    ga = rng.standard_normal(nt + 1)
+
+    def loss(Ev):
+        _, d, acc = oracle_mod.propagate(psi0, Ev, dx, dt, a, mask_values=m)
+        return float(np.dot(gd, d) + np.dot(ga, acc))
+
+    gE = oracle_mod.adjoint(psi0, E, dx, dt, a, gd, ga, mask_values=m)
+    for k in [0, 1, 17, 120, 239, 240]:
+        eps = 1e-5
+        Ep, Em = E.copy(), E.copy()
+        Ep[k] += eps
+        Em[k] -= eps
+        fd = (loss(Ep) - loss(Em)) / (2 * eps)
+        assert abs(fd - gE[k]) < 1e-6 * (abs(fd) + 1e-3), (k, fd, gE[k])
+    # directional derivative along a random field perturbation
+    v = rng.standard_normal(nt + 1)
+    eps = 1e-6
+    fd = (loss(E + eps * v) - loss(E - eps * v)) / (2 * eps)
+    assert abs(fd - np.dot(gE, v)) < 1e-6 * abs(fd)
