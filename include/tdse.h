@@ -173,6 +173,30 @@ tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);
 tdse_status tdse_set_launch(tdse_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
                             int32_t max_ctas);
 
+/* FULL_CN FP64 propagation that allocates nothing, for callers that cannot call cudaMalloc: code
+ * embedded in a host application that owns the whole device-memory budget (a pre-sized pool it
+ * hands out itself), or code on a path that must not allocate at all.  The paper has no
+ * counterpart; it is the same kernel as tdse_propagate with every piece of scratch (tables,
+ * scheduler state, group descriptors, solver rows) in one fixed 64 MiB array compiled into the
+ * library, which every GPU that loads the library holds until the process exits.
+ *   inst_host       one instance description shared by all n_inst instances (one grid class)
+ *   n_steps         Nt of every instance; row_stride: E, d and a hold row i at [i*row_stride, ...),
+ *                   element k of a row being sample n = sample_base + k
+ *   psi_dev         in/out, caller-owned, 32*ceil(n_inst/32)*N complex doubles (re, im) in the
+ *                   lane-interleaved layout: instance i, point j at complex index
+ *                   ((i/32)*N + j)*32 + i%32 (the padding lanes are never read or written)
+ *   other arguments as tdse_propagate; no non-finite flags are reported.
+ * Sizes whose scratch does not fit the array return TDSE_ERR_ARG with the limit in the message;
+ * up to that limit the grid is shrunk to what fits (fewer CTAs, so slower than tdse_propagate).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Every call shares the array and leaves its contents
+ * behind (the call clears what has to start at zero); calls that overlap on the GPU -- on
+ * different streams, or concurrent host threads -- race on it and must be serialised. */
+tdse_status tdse_propagate_static(const tdse_instance* inst_host, int64_t n_inst, double dt,
+                                  const tdse_absorber* absorber, int64_t n_steps, int64_t row_stride,
+                                  double* psi_dev, const double* E_dev, double* d_dev, double* a_dev,
+                                  int64_t sample_base, int64_t step_begin, int64_t step_end, void* stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* tdse_last_error(void);
 

@@ -20,7 +20,8 @@ _lib = None
 
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
-           "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_last_error")
+           "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
+           "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -69,6 +70,9 @@ def load(path: str | None = None):
     L.tdse_spectrum.argtypes = [_vp, _i64p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _vp, _vp]
     L.tdse_plan.argtypes = [_vp, ctypes.POINTER(tdse_plan_info)]
     L.tdse_set_launch.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.tdse_propagate_static.argtypes = [ctypes.POINTER(tdse_instance), ctypes.c_int64, ctypes.c_double,
+                                        ctypes.POINTER(tdse_absorber), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
+                                        _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -234,3 +238,13 @@ def spectrum(a, offsets, dt, k_begin, k_end, out=None, stream=None):
                                 int(k_end), _dev_ptr(out, "S"), _stream_ptr(stream)))
     return out
 
+
+def tdse_propagate_static(inst, n_inst, dt, n_steps, row_stride, psi, E, d, a, step_begin, step_end, sample_base=0,
+                          absorber=(20.0, 0.125), stream=None):
+    """Allocation-free propagation (see include/tdse.h).  inst = (N, dx, softening, charge); psi is a
+    float64 device tensor holding the lane-interleaved wavefunctions, 2 * 32 * ceil(n_inst/32) * N values."""
+    ab = None if absorber is None else ctypes.byref(tdse_absorber(float(absorber[0]), float(absorber[1])))
+    ins = tdse_instance(int(inst[0]), float(inst[1]), float(inst[2]), float(inst[3]))
+    _check(load().tdse_propagate_static(ctypes.byref(ins), int(n_inst), float(dt), ab, int(n_steps), int(row_stride),
+                                        _dev_ptr(psi, "psi"), _dev_ptr(E, "E"), _dev_ptr(d, "d"), _dev_ptr(a, "a"),
+                                        int(sample_base), int(step_begin), int(step_end), _stream_ptr(stream)))
