@@ -41,8 +41,9 @@ FLOPS_PER_POINT_STEP = 48.0          # algorithmic FULL_CN work per grid-point s
 FP64_FMA_PER_CLK_PER_SM = 2.0        # GB300 FP64 pipe: 2 FMA/clk/SM (1.2 TFLOP/s measured at 2.0 GHz)
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_propagate_fp64_volume_traffic.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_2507_04115_gb300", "csrc", "tdse_propagate.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_propagate_full_cn_fp64_volume_traffic.txt")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2507_04115_gb300", "csrc", f)
+               for f in ("tdse_full_cn.cu", "tdse_sched.cuh", "tdse_device.cuh")]
 
 
 def parse_args():
@@ -60,6 +61,8 @@ def parse_args():
     p.add_argument("--slice", type=int, default=0, help="override time steps per scheduling slice")
     p.add_argument("--instances", type=int, default=8192, help="instances per GPU (smaller = profiling case)")
     p.add_argument("--nt", type=int, default=0, help="propagate only the first nt steps (0 = whole pulse)")
+    p.add_argument("--mixed-compare", type=int, default=1,
+                   help="also time the MIXED path on two chunks and propagate the oracle sample in MIXED")
     return p.parse_args()
 
 
@@ -115,6 +118,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_sha():
+    """sha256 over the sources of the FULL_CN kernel (kernel, scheduler and device helpers)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic_per_point_step():
     """DRAM bytes per grid-point step of k_propagate_fp64 from the committed ncu summary, or None
     when the summary is missing or the kernel source changed since the capture."""
@@ -125,7 +136,7 @@ def kernel_traffic_per_point_step():
         if ":" in line:
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    sha = kernel_source_sha()
     if kv.get("source_sha256") != sha:
         return None
     try:
@@ -359,15 +370,60 @@ def own_arm(args):
         spec_err = {"instances": len(sample_idx), "rel_l2_max": max(l2s), "harmonic_rel_max": max(worst),
                     "a_series_rel_max": series, "q_cut": q_cut, "bound": 1e-6}
 
+    # mixed precision on the same workload: throughput over two chunks of the whole batch, and the
+    # spectral error of the oracle sample propagated in full (one group, so it runs on one SM)
+    mixed = None
+    if args.mixed_compare and world == 1:
+        batch.close()
+        mb = tdse.Batch([N] * n, dx, a_soft, [Nt] * n, dt, row_offsets=offs,
+                        absorber=(full.mask_width, full.mask_exponent), precision=tdse.TDSE_MIXED, device=local_rank)
+        mb.ground_state()
+        n_m = min(2, n_chunks)
+        mb.propagate(Ec[0], dc[0], ac[0], chunks[0][0], chunks[0][1], sample_base=chunks[0][0], stream=stream)
+        torch.cuda.synchronize(dev)
+        e0_ = torch.cuda.Event(enable_timing=True)
+        e1_ = torch.cuda.Event(enable_timing=True)
+        e0_.record(stream)
+        for c in range(1, 1 + n_m):
+            s0, s1 = chunks[c]
+            mb.propagate(Ec[c], dc[c], ac[c], s0, s1, sample_base=s0, stream=stream)
+        e1_.record(stream)
+        torch.cuda.synchronize(dev)
+        m_ms = e0_.elapsed_time(e1_)
+        m_val = float(n) * N * sum(chunks[c][1] - chunks[c][0] for c in range(1, 1 + n_m)) / (m_ms * 1e-3)
+        mixed = {"value": m_val, "unit": UNIT, "speedup_vs_fp64": m_val / value, "steps": n_m,
+                 "dtype": "psi f32, elimination recurrence and observable sums f64"}
+        mb.close()
+        if cpu_async is not None:
+            k = len(sample_idx)
+            Es = torch.from_numpy(np.concatenate([inputs.sin2_pulse(Nt, dt, E0[i], omega, ncyc, phi[i])
+                                                  for i in sample_idx])).to(dev)
+            ms_ = tdse.Batch([N] * k, dx, a_soft, [Nt] * k, dt, absorber=(full.mask_width, full.mask_exponent),
+                             precision=tdse.TDSE_MIXED, device=local_rank)
+            ms_.ground_state()
+            dm, am = torch.zeros_like(Es), torch.zeros_like(Es)
+            ms_.propagate(Es, dm, am, stream=stream)
+            Sm = tdse.spectrum(am, np.arange(k + 1) * L, dt, 0, k_max, stream=stream).cpu().numpy()
+            ms_.close()
+            l2s, worst = [], []
+            for j in range(k):
+                S_ref = oracle.spectrum(accs[j], dt)[:k_max]
+                l2, wv = spectral_errors(Sm[j], S_ref, omega, dt, L, q_cut)
+                l2s.append(l2)
+                worst.append(wv)
+            mixed["spectral_error"] = {"instances": k, "rel_l2_max": max(l2s), "harmonic_rel_max": max(worst)}
+
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     pts_per_launch = float(n) * N * (timed_steps / args.steps)
     achieved = FLOPS_PER_POINT_STEP * pts_per_launch / avg_launch_s
     peak = FP64_FMA_PER_CLK_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6
     tpp = kernel_traffic_per_point_step()
+    pipes = tdse.tdse_probe_pipes(local_rank)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tpp * pts_per_launch) if tpp is not None else None,
-                "kernel": "k_propagate_fp64", "pipe": "fp64",
+                "kernel": "k_propagate_full_cn<fp64>", "pipe": "fp64",
                 "peak_how": "2 FP64 FMA/clk/SM x 152 SMs x 2 flops x 2070 MHz (unit counts at max clock)",
+                "fp64_fma_measured_tflops": pipes["fp64_fma_tflops"],
                 "achieved_how": "48 flops per grid-point step x points x steps per launch / mean CUDA-event "
                                 "launch time"}
 
@@ -389,7 +445,7 @@ def own_arm(args):
            "gpu_launches": args.steps, "nonfinite_instance": bad,
            "setup": {"softening_fit_s": t_fit, "softening": a_soft, "ground_state_ms": t_gs_ms,
                      "spectrum_ms": t_spec_ms, "spectrum_bins": k_max},
-           "spectral_error": spec_err}
+           "spectral_error": spec_err, "mixed": mixed}
     if rank == 0:
         print(json.dumps(out), flush=True)
     batch.close()

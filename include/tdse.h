@@ -132,6 +132,26 @@ tdse_status tdse_propagate(tdse_batch* batch, const double* E_dev, double* d_dev
 tdse_status tdse_get_psi(tdse_batch* batch, int64_t inst, double* psi_dev, void* stream);
 tdse_status tdse_set_psi(tdse_batch* batch, int64_t inst, const double* psi_dev, void* stream);
 
+/* Copy the whole wavefunction state of the batch to (direction 0) or from (direction 1) a caller
+ * device buffer of tdse_plan's psi_bytes bytes (layout internal to the library; use it to
+ * checkpoint and resume a batch).  Loading marks the batch as initialised. */
+tdse_status tdse_copy_state(tdse_batch* batch, void* buffer_dev, int32_t direction, void* stream);
+
+/* Gradient of a loss L(d, a) with respect to every field sample, through the FULL_CN propagation
+ * (FP64 batches): the exact discrete adjoint of the scheme, i.e. the backward sweep with the
+ * conjugate-transposed step.  The batch's current wavefunctions are taken as the initial state
+ * psi^0 (call after tdse_ground_state, tdse_set_psi or tdse_copy_state, before propagating), and
+ * are left unchanged.  The loss gradients gd_n = dL/dd_n and ga_n = dL/da_n, the field E and the
+ * output gE_n = dL/dE_n use the batch's row layout with sample_base 0 and n = 0..Nt_i.
+ *   ckpt_every  states are checkpointed every ckpt_every steps and recomputed in between (one
+ *               interval of states is kept per CTA); memory ~ (Nt/ckpt_every + ckpt_every) states.
+ * With lambda^n = 2 dL/d conj(psi^n): lambda^Nt = g^Nt; mu = B_n^{-1} M lambda^{n+1};
+ * lambda^n = A_n mu + g^n, g^n_j = 2 dx (gd_n x_j + ga_n (dV_j + E_n)) psi^n_j; and
+ * dL/dEbar_n = dt/2 sum_j x_j Im(conj(mu_j)(psi^n_j + psi~^{n+1}_j)) split evenly to E_n, E_{n+1},
+ * plus ga_n dx sum_j |psi^n_j|^2 on E_n (A_n = 1 + i dt/2 H(Ebar_n), B_n = conj(A_n), M the mask). */
+tdse_status tdse_adjoint(tdse_batch* batch, const double* E_dev, const double* gd_dev, const double* ga_dev,
+                         double* gE_dev, int32_t ckpt_every, void* stream);
+
 /* Synchronise the stream and report TDSE_ERR_NONFINITE if any instance's norm became non-finite
  * or exceeded 1 + 1e-6 (FP64; 1 + 1e-3 in MIXED) during a propagation since the batch was created
  * or last checked;
@@ -196,6 +216,25 @@ tdse_status tdse_propagate_static(const tdse_instance* inst_host, int64_t n_inst
                                   const tdse_absorber* absorber, int64_t n_steps, int64_t row_stride,
                                   double* psi_dev, const double* E_dev, double* d_dev, double* a_dev,
                                   int64_t sample_base, int64_t step_begin, int64_t step_end, void* stream);
+
+/* Measured rates of the arithmetic pipes the engine is bound by (the FP64 pipe of GB300 is not in a
+ * copy/GEMM peak table): FP64 and FP32 fused multiply-add throughput with every SM busy, FP64 warp
+ * instructions per second with one active lane per warp (the cost is per warp instruction), FP64
+ * throughput with 1, 2 and 4 warps per SM (one FP64 unit per SM sub-partition), and
+ * double->float->double conversion pairs per second.  Runs a few short bounded launches on
+ * `device` (synchronous; allocates a small buffer). */
+typedef struct {
+    double fp64_fma_tflops;
+    double fp64_warp_instr_per_s;
+    double fp64_one_lane_warp_instr_per_s;
+    double fp64_tflops_warps_per_sm[3];
+    double fp32_fma_tflops;
+    double cvt_pairs_per_s;
+    int32_t sm_count;
+    double sm_clock_mhz;
+} tdse_pipe_rates;
+
+tdse_status tdse_probe_pipes(int device, tdse_pipe_rates* out_host);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* tdse_last_error(void);

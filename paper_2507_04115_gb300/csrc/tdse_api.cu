@@ -112,6 +112,13 @@ struct tdse_batch {
     double* d_gs_energy = nullptr;
     int64_t* d_gs_iters = nullptr;
     int64_t psi_elems = 0, scratch_elems = 0;
+    // adjoint buffers (allocated on the first tdse_adjoint call, resized when the interval changes)
+    void* d_lam = nullptr;
+    void* d_ckpt = nullptr;
+    int64_t* d_ckpt_off = nullptr;
+    void* d_work = nullptr;
+    void* d_tape = nullptr;
+    int adj_kc = 0, adj_ctas = 0;
     int mixed() const { return precision == TDSE_MIXED ? 1 : 0; }
     size_t cx_bytes() const { return precision == TDSE_MIXED ? sizeof(float2) : sizeof(double2); }
 };
@@ -135,6 +142,13 @@ void free_device(tdse_batch* b)
     cudaFree(b->d_gs_off);
     cudaFree(b->d_gs_energy);
     cudaFree(b->d_gs_iters);
+    cudaFree(b->d_lam);
+    cudaFree(b->d_ckpt);
+    cudaFree(b->d_ckpt_off);
+    cudaFree(b->d_work);
+    cudaFree(b->d_tape);
+    b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
+    b->d_ckpt_off = nullptr;
     b->d_cls = nullptr;
     b->d_groups = nullptr;
     b->d_tab = nullptr;
@@ -602,6 +616,76 @@ tdse_status tdse_check(tdse_batch* b, int64_t* first_bad, void* stream)
         if (flags[b->slot_of_inst[i]]) bad = i;
     if (first_bad) *first_bad = bad;
     if (bad >= 0) return fail(TDSE_ERR_NONFINITE, "instance " + std::to_string(bad) + ": norm non-finite or above its rounding allowance");
+    return TDSE_OK;
+}
+
+tdse_status tdse_copy_state(tdse_batch* b, void* buffer_dev, int32_t direction, void* stream)
+{
+    if (!b || !buffer_dev) return fail(TDSE_ERR_ARG, "tdse_copy_state: NULL argument");
+    if (direction != 0 && direction != 1) return fail(TDSE_ERR_ARG, "tdse_copy_state: direction must be 0 or 1");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    const size_t bytes = (size_t)b->psi_elems * b->cx_bytes();
+    if (direction == 0)
+        TDSE_CUDA(cudaMemcpyAsync(buffer_dev, b->d_psi, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "tdse_copy_state");
+    else {
+        TDSE_CUDA(cudaMemcpyAsync(b->d_psi, buffer_dev, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "tdse_copy_state");
+        b->initialized = true;
+    }
+    return TDSE_OK;
+}
+
+tdse_status tdse_adjoint(tdse_batch* b, const double* E_dev, const double* gd_dev, const double* ga_dev, double* gE_dev,
+                         int32_t ckpt_every, void* stream)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_adjoint: NULL batch");
+    if (!E_dev || !gd_dev || !ga_dev || !gE_dev) return fail(TDSE_ERR_ARG, "tdse_adjoint: NULL buffer");
+    if (b->precision != TDSE_FP64 || b->scheme != TDSE_FULL_CN)
+        return fail(TDSE_ERR_ARG, "tdse_adjoint: only FP64 FULL_CN batches have an adjoint");
+    if (ckpt_every < 1 || ckpt_every > 65536) return fail(TDSE_ERR_ARG, "tdse_adjoint: ckpt_every out of [1, 65536]");
+    if (!b->initialized) return fail(TDSE_ERR_STATE, "tdse_adjoint: no initial state");
+    for (int64_t i = 0; i < b->n_inst; ++i)
+        if (b->row_off[i + 1] - b->row_off[i] < b->n_steps[i] + 1)
+            return fail(TDSE_ERR_ARG, "tdse_adjoint: row of instance " + std::to_string(i) + " shorter than Nt + 1");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    int n_max = 1;
+    for (auto& G : b->groups) n_max = std::max(n_max, G.N);
+    if (!b->d_lam || b->adj_kc != ckpt_every || b->adj_ctas != b->ctas) {
+        TDSE_CUDA(cudaStreamSynchronize(st), "tdse_adjoint: synchronize");
+        cudaFree(b->d_lam);
+        cudaFree(b->d_ckpt);
+        cudaFree(b->d_ckpt_off);
+        cudaFree(b->d_work);
+        cudaFree(b->d_tape);
+        b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
+        b->d_ckpt_off = nullptr;
+        b->adj_kc = 0;
+        std::vector<int64_t> off(b->groups.size());
+        int64_t total = 0;
+        for (size_t g = 0; g < b->groups.size(); ++g) {
+            off[g] = total;
+            const int64_t n_int = (b->groups[g].nt_max + ckpt_every - 1) / ckpt_every;
+            total += (n_int + 1) * (int64_t)b->groups[g].N * kLanes;
+        }
+        const size_t cx = sizeof(double2);
+        TDSE_CUDA(cudaMalloc(&b->d_lam, (size_t)std::max<int64_t>(b->psi_elems, 1) * cx), "cudaMalloc(adjoint lambda)");
+        TDSE_CUDA(cudaMalloc(&b->d_ckpt, (size_t)std::max<int64_t>(total, 1) * cx), "cudaMalloc(adjoint checkpoints)");
+        TDSE_CUDA(dev_alloc(&b->d_ckpt_off, off.size()), "cudaMalloc(adjoint offsets)");
+        TDSE_CUDA(cudaMalloc(&b->d_work, (size_t)b->ctas * n_max * kLanes * cx), "cudaMalloc(adjoint work)");
+        TDSE_CUDA(cudaMalloc(&b->d_tape, (size_t)b->ctas * ckpt_every * (size_t)n_max * kLanes * cx),
+                  "cudaMalloc(adjoint tape)");
+        TDSE_CUDA(cudaMemcpy(b->d_ckpt_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice),
+                  "cudaMemcpy(adjoint offsets)");
+        b->adj_kc = ckpt_every;
+        b->adj_ctas = b->ctas;
+    }
+    TDSE_CUDA(launch_adjoint_full_cn(b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas, b->d_cls, b->d_tab,
+                                     b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_lam, b->d_ckpt, b->d_ckpt_off,
+                                     b->d_work, b->d_tape, b->d_scratch, b->rows, n_max, ckpt_every, E_dev, gd_dev,
+                                     ga_dev, gE_dev, b->mask_on, b->d_busy, b->d_progress, st),
+              "adjoint launch");
     return TDSE_OK;
 }
 

@@ -1,0 +1,297 @@
+// FULL_CN real-time propagation kernel of libtdse (sm_103a), FP64 and MIXED precision.
+//
+// Numerical scheme (one step t_n -> t_{n+1}, h = dt/2, Ebar = (E_n + E_{n+1})/2):
+//   A = 1 + i h H(Ebar) = tridiag(-i beta, 1 + i s_j, -i beta),  beta = dt/(4 dx^2),
+//   s_j = h (1/dx^2 + V_j + x_j Ebar);  psi^{n+1} = m (A^{-1}(1 - i h H) psi^n) = m (2 A^{-1} psi^n - psi^n)
+// because (1 - i h H) = 2 - A.  So each step is one tridiagonal solve A y = psi^n (Thomas: forward
+// elimination, back substitution) and a pointwise update -- no right-hand-side product.
+//
+// Parallel layout (lane-batched segmented Thomas):
+//   * a group = 32 instances of one grid class, one per lane, so every warp instruction works on
+//     32 independent systems (the FP64 pipe costs the same per warp instruction whatever the
+//     number of active lanes, so full warps matter);
+//   * a CTA of P warps owns one group at a time; warp w owns the grid segment [w m, (w+1) m);
+//   * a segment's sweep starts K points before the segment and closes K points after it.  A is
+//     strictly diagonally dominant with Re(pivot) >= 1, so both the forward coefficients and the
+//     back substitution forget their starting values by a factor <= beta per point; K is chosen so
+//     that beta^K < 1e-18, below double rounding.  The outermost segments use the exact walls.
+//   * scheduling: a persistent grid of CTAs picks groups dynamically, one time slice (a few tens
+//     of steps) at a time, always the free group with the most remaining slices.  A group is
+//     claimed with an atomic compare-and-swap and released after its slice; a CTA that finds no
+//     free unfinished group exits.  No CTA ever waits on another, so there is nothing to time out.
+//     Dynamic slices balance the load when the number of groups is not a multiple of the SM count
+//     (8192 instances = 256 groups on 152 SMs) and when groups have different lengths.
+// HBM layouts: psi [group][j][lane] (16 B per point, a warp reads 512 contiguous bytes), scratch per
+// CTA [warp][row][gamma | D][lane].
+#include "tdse_sched.cuh"
+
+namespace tdse {
+
+template <bool kMixed>
+__global__ void __launch_bounds__(512, 1)
+k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const ClassDesc* __restrict__ cls,
+                    const double* __restrict__ tab, const int64_t* __restrict__ slot_row,
+                    const int64_t* __restrict__ slot_nt, void* __restrict__ psi_raw, void* __restrict__ scratch_raw,
+                    int rows, const double* __restrict__ E, double* __restrict__ d_out, double* __restrict__ a_out,
+                    int64_t sample_base, int64_t step_begin, int64_t step_end, int slice, int mask_on,
+                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status)
+{
+    using R = typename Prec<kMixed>::R;
+    using Cx = typename Prec<kMixed>::C;
+    extern __shared__ double red[];   // [P][3][32]
+    __shared__ int s_g, s_k;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int P = blockDim.x >> 5;
+    Cx* __restrict__ psi_all = static_cast<Cx*>(psi_raw);
+    Cx* __restrict__ sc = static_cast<Cx*>(scratch_raw) + ((int64_t)blockIdx.x * P + w) * rows * (2 * kLanes);
+
+    for (;;) {
+        if (w == 0) {
+            int k = 0;
+            const int g = pick_group(groups, n_groups, busy, progress, step_begin, step_end, slice, &k);
+            if (lane == 0) {
+                s_g = g;
+                s_k = k;
+            }
+        }
+        __syncthreads();
+        const int g = s_g;
+        const int kslice = s_k;
+        __threadfence();   // order this CTA's reads of the group's psi after the claim
+        __syncthreads();   // s_g / s_k are rewritten only after every warp has read them
+        if (g < 0) break;
+
+        const GroupDesc G = groups[g];
+        const ClassDesc C = cls[G.cls];
+        const int N = G.N, Pg = G.P, K = G.K, m = G.m;
+        const int64_t slot = G.slot0 + lane;
+        const int64_t nt = slot_nt[slot];   // -1 for padding lanes
+        const int64_t row = slot_row[slot];
+        const double beta = C.beta;
+        const double inv_beta = 1.0 / beta;
+        const R two_over_beta = (R)(2.0 / beta);
+        const double dx = C.dx;
+        // warps beyond the group's segment count own an empty segment
+        const int s = w < Pg ? min(N, w * m) : N;
+        const int e = w < Pg ? min(N, s + m) : N;
+        const int lo = w < Pg ? max(0, s - K) : N;
+        const int hi = w < Pg ? min(N, e + K) : N;
+        Cx* __restrict__ ps = psi_all + G.psi_off;
+        const double2* __restrict__ tab_ab2 = reinterpret_cast<const double2*>(tab + tab_ab(C));
+        const double2* __restrict__ tab_xv2 = reinterpret_cast<const double2*>(tab + tab_xv(C));
+        const double* __restrict__ tab_m = tab + tab_mk(C);
+        const int jm_lo = mask_on ? C.jm_lo : 0;
+        const int jm_hi = mask_on ? C.jm_hi : N - 1;
+        const int64_t n_end = min(step_end, G.nt_max);
+        const int64_t n0 = step_begin + (int64_t)kslice * slice;
+        const int64_t n1 = min(n_end, n0 + slice);
+
+        if (kslice == 0 && step_begin == 0) {
+            // observables of the initial state
+            ObsSums o{0.0, 0.0, 0.0};
+            for (int j = s; j < e; ++j) {
+                const Cx p = ld_cg(ps + (int64_t)j * kLanes + lane);
+                const double rho = fma((double)p.x, (double)p.x, (double)p.y * (double)p.y);
+                const double2 xv = __ldg(tab_xv2 + j);
+                o.n += rho;
+                o.x = fma(xv.x, rho, o.x);
+                o.v = fma(xv.y, rho, o.v);
+            }
+            const ObsSums t = reduce_obs(o, red, P);
+            if (w == 0 && nt >= 0) {
+                const double E0 = E[row - sample_base];
+                d_out[row - sample_base] = t.x * dx;
+                a_out[row - sample_base] = fma(E0, t.n, t.v) * dx;
+            }
+            __syncthreads();
+        }
+
+        for (int64_t n = n0; n < n1; ++n) {
+            const bool active = n < nt;
+            double En = 0.0, En1 = 0.0;
+            if (active) {
+                En = E[row + n - sample_base];
+                En1 = E[row + n + 1 - sample_base];
+            }
+            const double Eb = 0.5 * (En + En1);
+
+            // Forward elimination over [lo, hi) in scaled variables: Q = q/beta with
+            // q_j = 1 + i s_j + beta^2 g_{j-1} the Thomas pivot, gamma = i beta g = i conj(Q)/|Q|^2,
+            // D = beta d = -i gamma u with u = psi + i D_{j-1}.  Tables hold s_j/beta split as
+            // (S0_j, Xh_j)/beta; Re Q = 1/beta + Im gamma_{j-1}, Im Q = s_j/beta - Re gamma_{j-1}.
+            // The recurrence for Q and gamma always runs in double.
+            double cr = 0.0, ci = 0.0;
+            R Dr = 0, Di = 0;
+            {
+                const Cx* pj = ps + (int64_t)lo * kLanes + lane;
+                Cx pa = lo < hi ? ld_cg(pj) : mk(R(0), R(0));
+                Cx pb = lo + 1 < hi ? ld_cg(pj + kLanes) : mk(R(0), R(0));
+                Cx* r = sc;
+#pragma unroll 2
+                for (int j = lo; j < hi; ++j) {
+                    const Cx p = pa;
+                    pa = pb;
+                    if (j + 2 < hi) pb = ld_cg(ps + (int64_t)(j + 2) * kLanes + lane);
+                    const double2 t = __ldg(tab_ab2 + j);
+                    const double Qr = inv_beta + ci;
+                    const double Qi = fma(t.y, Eb, t.x) - cr;
+                    const double inv = rcp_pos(fma(Qr, Qr, Qi * Qi));
+                    cr = Qi * inv;
+                    ci = Qr * inv;
+                    R gr, gi;
+                    if constexpr (kMixed) {
+                        gr = d2f(cr);
+                        gi = d2f(ci);
+                    } else {
+                        gr = cr;
+                        gi = ci;
+                    }
+                    const R ur = p.x - Di;
+                    const R ui = p.y + Dr;
+                    Dr = fma(gr, ui, gi * ur);
+                    Di = fma(gi, ui, -gr * ur);
+                    r[lane] = mk(gr, gi);
+                    r[kLanes + lane] = mk(Dr, Di);
+                    r += 2 * kLanes;
+                }
+            }
+            __syncthreads();   // every read of psi^n (own segment and halos) precedes any write of psi^{n+1}
+
+            // Back substitution Y_j = D_j + gamma_j Y_{j+1} (Y = beta y), seeded with 0 at hi (exact at
+            // the wall), then psi^{n+1}_j = m_j (2 Y_j / beta - psi^n_j) on the own segment.
+            R Yr = 0, Yi = 0;
+            ObsSums o{0.0, 0.0, 0.0};
+            {
+                const Cx* r = sc + (int64_t)(hi - 1 - lo) * (2 * kLanes);
+                for (int j = hi - 1; j >= e; --j) {
+                    const Cx g2 = r[lane];
+                    const Cx d2 = r[kLanes + lane];
+                    r -= 2 * kLanes;
+                    const R nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
+                    Yi = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
+                    Yr = nr;
+                }
+                // own segment, with the scratch row and the old psi prefetched two points ahead
+                Cx ga = mk(R(0), R(0)), da = ga, gb = ga, db = ga, pa = ga, pb = ga;
+                if (e - 1 >= s) {
+                    ga = r[lane];
+                    da = r[kLanes + lane];
+                    pa = ld_cg(ps + (int64_t)(e - 1) * kLanes + lane);
+                }
+                if (e - 2 >= s) {
+                    gb = r[-2 * kLanes + lane];
+                    db = r[-kLanes + lane];
+                    pb = ld_cg(ps + (int64_t)(e - 2) * kLanes + lane);
+                }
+                // MIXED: |psi|^2 and its weighted sums run in float over blocks of 8 points, each
+                // block total is added to the double accumulators
+                R fn = 0, fx = 0, fv = 0;
+                int blk = 0;
+#pragma unroll 2
+                for (int j = e - 1; j >= s; --j) {
+                    const Cx g2 = ga, d2 = da, old = pa;
+                    ga = gb;
+                    da = db;
+                    pa = pb;
+                    if (j - 2 >= s) {
+                        gb = r[-4 * kLanes + lane];
+                        db = r[-3 * kLanes + lane];
+                        pb = ld_cg(ps + (int64_t)(j - 2) * kLanes + lane);
+                    }
+                    r -= 2 * kLanes;
+                    const R nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
+                    Yi = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
+                    Yr = nr;
+                    R xr = fma(two_over_beta, Yr, -old.x);
+                    R xi = fma(two_over_beta, Yi, -old.y);
+                    if (j < jm_lo || j > jm_hi) {
+                        const R mm = (R)__ldg(tab_m + j);
+                        xr *= mm;
+                        xi *= mm;
+                    }
+                    if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
+                    const R rho = fma(xr, xr, xi * xi);
+                    const double2 xv = __ldg(tab_xv2 + j);
+                    if constexpr (kMixed) {
+                        fn += rho;
+                        fx = fma((R)xv.x, rho, fx);
+                        fv = fma((R)xv.y, rho, fv);
+                        if (++blk == 8) {
+                            o.n += (double)fn;
+                            o.x += (double)fx;
+                            o.v += (double)fv;
+                            fn = fx = fv = 0;
+                            blk = 0;
+                        }
+                    } else {
+                        o.n += rho;
+                        o.x = fma(xv.x, rho, o.x);
+                        o.v = fma(xv.y, rho, o.v);
+                    }
+                }
+                if constexpr (kMixed) {
+                    o.n += (double)fn;
+                    o.x += (double)fx;
+                    o.v += (double)fv;
+                }
+            }
+            const ObsSums t = reduce_obs(o, red, P);   // its barrier also orders this step's psi writes
+            if (w == 0 && active) {
+                const int64_t kk = row + n + 1 - sample_base;
+                d_out[kk] = t.x * dx;
+                a_out[kk] = fma(En1, t.n, t.v) * dx;
+                // the norm never grows in exact arithmetic (unitary step, mask <= 1); the allowance
+                // covers rounding: 1e-6 in FP64, 1e-3 in MIXED where float psi random-walks ~1e-5
+                if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
+            }
+        }
+
+        // release the group: its psi writes become visible before the next owner's claim
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            *(volatile int*)(progress + g) = kslice + 1;
+            __threadfence();
+            atomicExch(busy + g, 0);
+        }
+    }
+}
+
+cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
+                                     const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
+                                     const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
+                                     const double* E, double* d_out, double* a_out, int64_t sample_base,
+                                     int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
+                                     int* d_progress, int* d_status, cudaStream_t st)
+{
+    if (n_groups == 0 || ctas == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(d_busy, 0, sizeof(int) * n_groups, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d_progress, 0, sizeof(int) * n_groups, st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)P * 3 * kLanes * sizeof(double);
+    if (mixed) {
+        k_propagate_full_cn<true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
+            d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status);
+    } else {
+        k_propagate_full_cn<false><<<(unsigned)ctas, P * kLanes, smem, st>>>(
+            d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status);
+    }
+    return cudaGetLastError();
+}
+
+int propagate_max_ctas_per_sm(int mixed, int P)
+{
+    int n = 0;
+    const size_t smem = (size_t)P * 3 * kLanes * sizeof(double);
+    const cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<true>, P * kLanes, smem)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<false>, P * kLanes, smem);
+    if (e != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace tdse

@@ -101,6 +101,16 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
                                      int* d_progress, int* d_status, cudaStream_t st);
 int propagate_max_ctas_per_sm(int mixed, int P);
 
+// Discrete adjoint of FULL_CN in FP64 (tdse_adjoint.cu): one CTA per group for the whole call.
+// lam: psi-shaped; ckpt: per group (intervals + 1) states at ckpt_off[g]; work: ctas * n_max * 32;
+// tape: ctas * kc * n_max * 32; scratch as for the propagation.
+cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, int P, int ctas, const ClassDesc* d_cls,
+                                   const double* d_tab, const int64_t* d_slot_row, const int64_t* d_slot_nt,
+                                   const void* d_psi0, void* d_lam, void* d_ckpt, const int64_t* d_ckpt_off,
+                                   void* d_work, void* d_tape, void* d_scratch, int rows, int n_max, int kc,
+                                   const double* E, const double* gd, const double* ga, double* gE, int mask_on,
+                                   int* d_busy, int* d_progress, cudaStream_t st);
+
 // Persistent NUMEROV_SPLIT propagation (same scheduler, scratch and layouts; tables nw/nl/nc/nf).
 cudaError_t launch_propagate_numerov(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
                                      const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,

@@ -1,0 +1,279 @@
+// NUMEROV_SPLIT real-time propagation kernel of libtdse (sm_103a), FP64 and MIXED precision.  It
+// shares the lane-batched layout, the halo-segmented sweeps and the persistent group scheduler of
+// the FULL_CN kernel (see tdse_full_cn.cu).
+#include "tdse_sched.cuh"
+
+namespace tdse {
+
+// NUMEROV_SPLIT step (the paper's three substeps, Sec. 4.2, Eqs. "CN - step 4/2/3"):
+//   psi1 = (M2 - i h K) psi,  psi2 = (M2 + i h K)^{-1} psi1,  psi3_j = exp(-i dt E_n x_j) psi2_j,
+// with K = -Delta2/2 + M2 V, M2 = tridiag(1, 10, 1)/12, h = dt/2.  Since A + B = 2 M2 for
+// A = M2 + i h K and B = M2 - i h K, psi2 = 2 A^{-1} (M2 psi) - psi: one solve with the
+// time-independent A, whose LU factors (W = 1/pivot folded with the 1/12 of M2, L, C) are tabulated
+// once per class in double.  Forward d_j = W_j (psi_{j-1} + 10 psi_j + psi_{j+1}) - L_j d_{j-1},
+// backward y_j = d_j - C_j y_{j+1}.  Segments start their sweeps K points early / close K points
+// late with the exact factors; both recurrences forget their truncated start by max|L|, max|C| per
+// point, and K is chosen from that bound.  Then psi^{n+1} = m exp(-i dt E_n x) (2y - psi).
+// The phase exp(-i dt E_n x_j) runs as a complex rotation from the segment end, re-seeded from
+// sincos every 64 points (double) or 8 points (float).
+template <bool kMixed>
+__global__ void __launch_bounds__(512, 1)
+k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, const ClassDesc* __restrict__ cls,
+                    const double* __restrict__ tab, const int64_t* __restrict__ slot_row,
+                    const int64_t* __restrict__ slot_nt, void* __restrict__ psi_raw, void* __restrict__ scratch_raw,
+                    int rows, const double* __restrict__ E, double* __restrict__ d_out, double* __restrict__ a_out,
+                    int64_t sample_base, int64_t step_begin, int64_t step_end, int slice, int mask_on, double dt,
+                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status)
+{
+    using R = typename Prec<kMixed>::R;
+    using Cx = typename Prec<kMixed>::C;
+    extern __shared__ double red[];   // [P][3][32]
+    __shared__ int s_g, s_k;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int P = blockDim.x >> 5;
+    Cx* __restrict__ psi_all = static_cast<Cx*>(psi_raw);
+    // scratch rows: d_j only (one complex per row per lane)
+    Cx* __restrict__ sc = static_cast<Cx*>(scratch_raw) + ((int64_t)blockIdx.x * P + w) * rows * (2 * kLanes);
+
+    for (;;) {
+        if (w == 0) {
+            int k = 0;
+            const int g = pick_group(groups, n_groups, busy, progress, step_begin, step_end, slice, &k);
+            if (lane == 0) {
+                s_g = g;
+                s_k = k;
+            }
+        }
+        __syncthreads();
+        const int g = s_g;
+        const int kslice = s_k;
+        __threadfence();
+        __syncthreads();
+        if (g < 0) break;
+
+        const GroupDesc G = groups[g];
+        const ClassDesc C = cls[G.cls];
+        const int N = G.N, Pg = G.P, K = G.K, m = G.m;
+        const int64_t slot = G.slot0 + lane;
+        const int64_t nt = slot_nt[slot];
+        const int64_t row = slot_row[slot];
+        const double dx = C.dx;
+        const int s = w < Pg ? min(N, w * m) : N;
+        const int e = w < Pg ? min(N, s + m) : N;
+        const int lo = w < Pg ? max(0, s - K) : N;
+        const int hi = w < Pg ? min(N, e + K) : N;
+        Cx* __restrict__ ps = psi_all + G.psi_off;
+        const double2* __restrict__ tab_xv2 = reinterpret_cast<const double2*>(tab + tab_xv(C));
+        const double* __restrict__ tab_m = tab + tab_mk(C);
+        const double2* __restrict__ tW = reinterpret_cast<const double2*>(tab + tab_nw(C));
+        const double2* __restrict__ tL = reinterpret_cast<const double2*>(tab + tab_nl(C));
+        const double2* __restrict__ tC = reinterpret_cast<const double2*>(tab + tab_nc(C));
+        const float2* __restrict__ tF = reinterpret_cast<const float2*>(tab + tab_nf(C));
+        const int jm_lo = mask_on ? C.jm_lo : 0;
+        const int jm_hi = mask_on ? C.jm_hi : N - 1;
+        const int64_t n_end = min(step_end, G.nt_max);
+        const int64_t n0 = step_begin + (int64_t)kslice * slice;
+        const int64_t n1 = min(n_end, n0 + slice);
+        const double x0 = -0.5 * (N - 1) * dx;
+
+        if (kslice == 0 && step_begin == 0) {
+            ObsSums o{0.0, 0.0, 0.0};
+            for (int j = s; j < e; ++j) {
+                const Cx p = ld_cg(ps + (int64_t)j * kLanes + lane);
+                const double rho = fma((double)p.x, (double)p.x, (double)p.y * (double)p.y);
+                const double2 xv = __ldg(tab_xv2 + j);
+                o.n += rho;
+                o.x = fma(xv.x, rho, o.x);
+                o.v = fma(xv.y, rho, o.v);
+            }
+            const ObsSums t = reduce_obs(o, red, P);
+            if (w == 0 && nt >= 0) {
+                const double E0 = E[row - sample_base];
+                d_out[row - sample_base] = t.x * dx;
+                a_out[row - sample_base] = fma(E0, t.n, t.v) * dx;
+            }
+            __syncthreads();
+        }
+
+        for (int64_t n = n0; n < n1; ++n) {
+            const bool active = n < nt;
+            double En = 0.0, En1 = 0.0;
+            if (active) {
+                En = E[row + n - sample_base];
+                En1 = E[row + n + 1 - sample_base];
+            }
+
+            // forward: d_j = W_j r_j - L_j d_{j-1}, r_j = psi_{j-1} + 10 psi_j + psi_{j+1}
+            {
+                const Cx zero = mk(R(0), R(0));
+                Cx pm = lo > 0 && lo < hi ? ld_cg(ps + (int64_t)(lo - 1) * kLanes + lane) : zero;
+                Cx pc = lo < hi ? ld_cg(ps + (int64_t)lo * kLanes + lane) : zero;
+                Cx pn = lo + 1 < N && lo < hi ? ld_cg(ps + (int64_t)(lo + 1) * kLanes + lane) : zero;
+                R dr = 0, di = 0;
+                Cx* r = sc;
+#pragma unroll 2
+                for (int j = lo; j < hi; ++j) {
+                    const Cx nx = (j + 2 < N && j + 1 < hi) ? ld_cg(ps + (int64_t)(j + 2) * kLanes + lane) : zero;
+                    const R rr = fma(R(10), pc.x, pm.x + pn.x);
+                    const R ri = fma(R(10), pc.y, pm.y + pn.y);
+                    R wr, wi, lr, li;
+                    if constexpr (kMixed) {
+                        const float2 fw = __ldg(tF + 3 * j), fl = __ldg(tF + 3 * j + 1);
+                        wr = fw.x; wi = fw.y; lr = fl.x; li = fl.y;
+                    } else {
+                        const double2 tw = __ldg(tW + j), tl = __ldg(tL + j);
+                        wr = tw.x; wi = tw.y; lr = tl.x; li = tl.y;
+                    }
+                    const R nr = fma(wr, rr, fma(-wi, ri, fma(-lr, dr, li * di)));
+                    const R ni = fma(wr, ri, fma(wi, rr, fma(-lr, di, -li * dr)));
+                    dr = nr;
+                    di = ni;
+                    r[lane] = mk(dr, di);
+                    r += 2 * kLanes;
+                    pm = pc;
+                    pc = pn;
+                    pn = nx;
+                }
+            }
+            __syncthreads();
+
+            // backward: y_j = d_j - C_j y_{j+1}; psi^{n+1}_j = m_j phase_j (2 y_j - psi^n_j)
+            ObsSums o{0.0, 0.0, 0.0};
+            {
+                R yr = 0, yi = 0;
+                const Cx* r = sc + (int64_t)(hi - 1 - lo) * (2 * kLanes);
+                for (int j = hi - 1; j >= e; --j) {
+                    const Cx d2 = r[0 + lane];
+                    r -= 2 * kLanes;
+                    R cr_, ci_;
+                    if constexpr (kMixed) {
+                        const float2 fc = __ldg(tF + 3 * j + 2);
+                        cr_ = fc.x; ci_ = fc.y;
+                    } else {
+                        const double2 tc = __ldg(tC + j);
+                        cr_ = tc.x; ci_ = tc.y;
+                    }
+                    const R nr = fma(-cr_, yr, fma(ci_, yi, d2.x));
+                    yi = fma(-cr_, yi, fma(-ci_, yr, d2.y));
+                    yr = nr;
+                }
+                // phase rotation per point: exp(+i dt E_n dx) steps x_j down by dx
+                R wr_, wi_;
+                if constexpr (kMixed) {
+                    sincosf((float)(dt * En * dx), &wi_, &wr_);
+                } else {
+                    sincos(dt * En * dx, &wi_, &wr_);
+                }
+                const R mdtE = (R)(-dt * En);
+                const R x0r = (R)x0, dxr = (R)dx;
+                R phr = 1, phi = 0;
+                const int reseed = kMixed ? 8 : 64;
+                R fn = 0, fx = 0, fv = 0;
+                int blk = 0;
+                for (int j = e - 1; j >= s; --j) {
+                    const Cx d2 = r[lane];
+                    r -= 2 * kLanes;
+                    R cr_, ci_;
+                    if constexpr (kMixed) {
+                        const float2 fc = __ldg(tF + 3 * j + 2);
+                        cr_ = fc.x; ci_ = fc.y;
+                    } else {
+                        const double2 tc = __ldg(tC + j);
+                        cr_ = tc.x; ci_ = tc.y;
+                    }
+                    const R nr = fma(-cr_, yr, fma(ci_, yi, d2.x));
+                    yi = fma(-cr_, yi, fma(-ci_, yr, d2.y));
+                    yr = nr;
+                    if (((e - 1 - j) % reseed) == 0) {
+                        if constexpr (kMixed) {
+                            sincosf(mdtE * fmaf((float)j, dxr, x0r), &phi, &phr);
+                        } else {
+                            sincos(-dt * En * (x0 + j * dx), &phi, &phr);
+                        }
+                    }
+                    const Cx old = ld_cg(ps + (int64_t)j * kLanes + lane);
+                    const R tr = fma(R(2), yr, -old.x);
+                    const R ti = fma(R(2), yi, -old.y);
+                    R xr = fma(tr, phr, -ti * phi);
+                    R xi = fma(tr, phi, ti * phr);
+                    // next point (x smaller by dx): phase times exp(+i dt E dx)
+                    const R qr = fma(phr, wr_, -phi * wi_);
+                    phi = fma(phr, wi_, phi * wr_);
+                    phr = qr;
+                    if (j < jm_lo || j > jm_hi) {
+                        const R mm = (R)__ldg(tab_m + j);
+                        xr *= mm;
+                        xi *= mm;
+                    }
+                    if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
+                    const R rho = fma(xr, xr, xi * xi);
+                    const double2 xv = __ldg(tab_xv2 + j);
+                    if constexpr (kMixed) {
+                        fn += rho;
+                        fx = fma((R)xv.x, rho, fx);
+                        fv = fma((R)xv.y, rho, fv);
+                        if (++blk == 8) {
+                            o.n += (double)fn;
+                            o.x += (double)fx;
+                            o.v += (double)fv;
+                            fn = fx = fv = 0;
+                            blk = 0;
+                        }
+                    } else {
+                        o.n += rho;
+                        o.x = fma(xv.x, rho, o.x);
+                        o.v = fma(xv.y, rho, o.v);
+                    }
+                }
+                if constexpr (kMixed) {
+                    o.n += (double)fn;
+                    o.x += (double)fx;
+                    o.v += (double)fv;
+                }
+            }
+            const ObsSums t = reduce_obs(o, red, P);
+            if (w == 0 && active) {
+                const int64_t kk = row + n + 1 - sample_base;
+                d_out[kk] = t.x * dx;
+                a_out[kk] = fma(En1, t.n, t.v) * dx;
+                if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
+            }
+        }
+
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            *(volatile int*)(progress + g) = kslice + 1;
+            __threadfence();
+            atomicExch(busy + g, 0);
+        }
+    }
+}
+
+cudaError_t launch_propagate_numerov(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
+                                     const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
+                                     const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
+                                     const double* E, double* d_out, double* a_out, int64_t sample_base,
+                                     int64_t step_begin, int64_t step_end, int slice, int mask_on, double dt,
+                                     int* d_busy, int* d_progress, int* d_status, cudaStream_t st)
+{
+    if (n_groups == 0 || ctas == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(d_busy, 0, sizeof(int) * n_groups, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d_progress, 0, sizeof(int) * n_groups, st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)P * 3 * kLanes * sizeof(double);
+    if (mixed)
+        k_propagate_numerov<true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
+            d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
+            sample_base, step_begin, step_end, slice, mask_on, dt, d_busy, d_progress, d_status);
+    else
+        k_propagate_numerov<false><<<(unsigned)ctas, P * kLanes, smem, st>>>(
+            d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
+            sample_base, step_begin, step_end, slice, mask_on, dt, d_busy, d_progress, d_status);
+    return cudaGetLastError();
+}
+
+}  // namespace tdse

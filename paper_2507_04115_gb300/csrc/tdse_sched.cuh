@@ -1,0 +1,135 @@
+// Helpers shared by the persistent propagation kernels of libtdse (sm_103a): precision traits,
+// the observable reduction and the dynamic group scheduler.
+#pragma once
+
+#include "tdse_device.cuh"
+#include "tdse_internal.h"
+
+namespace tdse {
+
+
+// Storage and arithmetic types per precision: FP64 keeps everything in double; MIXED keeps psi,
+// the solve's right-hand side and back substitution, and the pointwise update in float, while the
+// elimination recurrence (the pivots and gamma) and the observable sums stay in double.
+template <bool kMixed> struct Prec;
+template <> struct Prec<false> {
+    using R = double;
+    using C = double2;
+};
+template <> struct Prec<true> {
+    using R = float;
+    using C = float2;
+};
+
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+
+// double -> float on the integer pipe for values well inside float's normal range: on GB300 a
+// hardware conversion costs as much as an FP64 multiply-add.  The 52-bit mantissa is rounded to 23
+// bits to nearest (ties away from zero; a carry into the exponent is the correct result), so the
+// rounding is unbiased -- truncation would perturb every step's elimination coefficients in the
+// same direction and the error would grow linearly with the number of steps.  Values outside the
+// range (including 0) take the hardware conversion.
+__device__ __forceinline__ float d2f(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    if (e - 897u < 253u) {
+        const unsigned bits = ((unsigned)hi & 0x80000000u) | ((e - 896u) << 23) | (((unsigned)hi & 0xfffffu) << 3) |
+                              (lo >> 29);
+        return __uint_as_float(bits + ((lo >> 28) & 1u));
+    }
+    return __double2float_rn(x);
+}
+
+struct ObsSums {
+    double n, x, v;
+};
+
+// Per-warp partial sums of |psi|^2, x |psi|^2 and dV/dx |psi|^2 combined over the CTA's warps
+// through shared memory; warp 0 receives the totals (the barrier inside also orders the psi
+// writes of the step before any read of the next one).
+__device__ __forceinline__ ObsSums reduce_obs(ObsSums s, double* red, int P)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    red[(w * 3 + 0) * 32 + lane] = s.n;
+    red[(w * 3 + 1) * 32 + lane] = s.x;
+    red[(w * 3 + 2) * 32 + lane] = s.v;
+    __syncthreads();
+    ObsSums t{0.0, 0.0, 0.0};
+    if (w == 0) {
+        for (int q = 0; q < P; ++q) {
+            t.n += red[(q * 3 + 0) * 32 + lane];
+            t.x += red[(q * 3 + 1) * 32 + lane];
+            t.v += red[(q * 3 + 2) * 32 + lane];
+        }
+    }
+    return t;
+}
+
+__device__ __forceinline__ int64_t group_slices(const GroupDesc& G, int64_t step_begin, int64_t step_end, int slice)
+{
+    const int64_t n_end = min(step_end, G.nt_max);
+    if (n_end > step_begin) return (n_end - step_begin + slice - 1) / slice;
+    return step_begin == 0 ? 1 : 0;   // only the initial observables
+}
+
+// Warp 0 picks and claims the free group with the most remaining slices; ties go to the group
+// closest after this CTA's index (cyclically), so that CTAs starting together claim different
+// groups instead of all racing for the same one.  Returns the group (its slice index in *k_out) or
+// -1 when no free unfinished group is left.  Every failed claim means another CTA claimed a group,
+// so the retries are bounded by the total number of claims.
+__device__ __forceinline__ int pick_group(const GroupDesc* groups, int64_t n_groups, int* busy, int* progress, int64_t step_begin,
+                          int64_t step_end, int slice, int* k_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t me = (int64_t)blockIdx.x % n_groups;
+    for (int64_t attempt = 0; attempt < 4 * n_groups + 64; ++attempt) {
+        int64_t best_rem = 0, best_d = n_groups, best_g = -1;
+        for (int64_t g = lane; g < n_groups; g += 32) {
+            const int64_t rem = group_slices(groups[g], step_begin, step_end, slice) -
+                                *(volatile int*)(progress + g);
+            const int64_t dist = (g - me + n_groups) % n_groups;
+            if (rem > 0 && *(volatile int*)(busy + g) == 0 && (rem > best_rem || (rem == best_rem && dist < best_d))) {
+                best_rem = rem;
+                best_d = dist;
+                best_g = g;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t r2 = __shfl_xor_sync(0xffffffffu, best_rem, o);
+            const int64_t d2 = __shfl_xor_sync(0xffffffffu, best_d, o);
+            const int64_t g2 = __shfl_xor_sync(0xffffffffu, best_g, o);
+            if (g2 >= 0 && (best_g < 0 || r2 > best_rem || (r2 == best_rem && d2 < best_d))) {
+                best_rem = r2;
+                best_d = d2;
+                best_g = g2;
+            }
+        }
+        if (best_g < 0) return -1;
+        int got = 0, k = 0;
+        if (lane == 0) {
+            if (atomicCAS(busy + best_g, 0, 1) == 0) {
+                __threadfence();   // acquire: the previous owner's psi writes precede its release
+                k = *(volatile int*)(progress + best_g);
+                if (k < group_slices(groups[best_g], step_begin, step_end, slice)) {
+                    got = 1;
+                } else {           // finished in the meantime: give it back
+                    atomicExch(busy + best_g, 0);
+                }
+            }
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (got) {
+            *k_out = k;
+            return (int)best_g;
+        }
+    }
+    return -1;
+}
+
+
+}  // namespace tdse

@@ -21,7 +21,7 @@ _lib = None
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
-           "tdse_last_error")
+           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -37,6 +37,13 @@ class tdse_plan_info(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int64), ("segments", ctypes.c_int32), ("halo", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas", ctypes.c_int32), ("slice_steps", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64), ("psi_bytes", ctypes.c_int64)]
+
+
+class tdse_pipe_rates(ctypes.Structure):
+    _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp64_warp_instr_per_s", ctypes.c_double),
+                ("fp64_one_lane_warp_instr_per_s", ctypes.c_double),
+                ("fp64_tflops_warps_per_sm", ctypes.c_double * 3), ("fp32_fma_tflops", ctypes.c_double),
+                ("cvt_pairs_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32), ("sm_clock_mhz", ctypes.c_double)]
 
 
 class TDSEError(RuntimeError):
@@ -73,6 +80,9 @@ def load(path: str | None = None):
     L.tdse_propagate_static.argtypes = [ctypes.POINTER(tdse_instance), ctypes.c_int64, ctypes.c_double,
                                         ctypes.POINTER(tdse_absorber), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
                                         _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp]
+    L.tdse_probe_pipes.argtypes = [ctypes.c_int, ctypes.POINTER(tdse_pipe_rates)]
+    L.tdse_copy_state.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
+    L.tdse_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -221,6 +231,26 @@ class Batch:
                     warps_per_cta=info.warps_per_cta, ctas=info.ctas, slice_steps=info.slice_steps,
                     scratch_bytes=info.scratch_bytes, psi_bytes=info.psi_bytes)
 
+    def save_state(self, stream=None):
+        """Device copy of every wavefunction (opaque layout; see tdse_copy_state)."""
+        import torch
+        buf = torch.empty(self.plan()["psi_bytes"] // 8, dtype=torch.float64, device=torch.device("cuda", self.device))
+        _check(load().tdse_copy_state(self._h, _dev_ptr(buf, "state"), 0, _stream_ptr(stream)))
+        return buf
+
+    def load_state(self, buf, stream=None):
+        _check(load().tdse_copy_state(self._h, _dev_ptr(buf, "state"), 1, _stream_ptr(stream)))
+
+    def adjoint(self, E, gd, ga, gE=None, ckpt_every=256, stream=None):
+        """dL/dE for loss gradients gd = dL/dd, ga = dL/da (device tensors in the row layout,
+        sample_base 0), from the batch's current state as psi^0 (see tdse_adjoint)."""
+        import torch
+        if gE is None:
+            gE = torch.zeros_like(E)
+        _check(load().tdse_adjoint(self._h, _dev_ptr(E, "E"), _dev_ptr(gd, "gd"), _dev_ptr(ga, "ga"),
+                                   _dev_ptr(gE, "gE"), int(ckpt_every), _stream_ptr(stream)))
+        return gE
+
     def set_launch(self, warps_per_cta=0, ctas_per_sm=0, slice_steps=0, max_ctas=0):
         """Override the persistent grid (see tdse_set_launch); 0 keeps a default."""
         _check(load().tdse_set_launch(self._h, int(warps_per_cta), int(ctas_per_sm), int(slice_steps),
@@ -248,3 +278,56 @@ def tdse_propagate_static(inst, n_inst, dt, n_steps, row_stride, psi, E, d, a, s
     _check(load().tdse_propagate_static(ctypes.byref(ins), int(n_inst), float(dt), ab, int(n_steps), int(row_stride),
                                         _dev_ptr(psi, "psi"), _dev_ptr(E, "E"), _dev_ptr(d, "d"), _dev_ptr(a, "a"),
                                         int(sample_base), int(step_begin), int(step_end), _stream_ptr(stream)))
+
+
+def tdse_probe_pipes(device=0):
+    """Measured FP64/FP32 pipe rates of the device (see include/tdse.h) as a dict."""
+    r = tdse_pipe_rates()
+    _check(load().tdse_probe_pipes(int(device), ctypes.byref(r)))
+    return dict(fp64_fma_tflops=r.fp64_fma_tflops, fp64_warp_instr_per_s=r.fp64_warp_instr_per_s,
+                fp64_one_lane_warp_instr_per_s=r.fp64_one_lane_warp_instr_per_s,
+                fp64_tflops_warps_per_sm=list(r.fp64_tflops_warps_per_sm), fp32_fma_tflops=r.fp32_fma_tflops,
+                cvt_pairs_per_s=r.cvt_pairs_per_s, sm_count=r.sm_count, sm_clock_mhz=r.sm_clock_mhz)
+
+
+def _make_autograd():
+    import torch
+
+    class TDSEPropagate(torch.autograd.Function):
+        """(d, a) = propagate(E) for an FP64 FULL_CN batch, differentiable with respect to the field
+        samples E through the library's adjoint kernel.  The batch must hold the initial state; it is
+        restored after the forward pass so that the backward pass starts from the same psi^0."""
+
+        @staticmethod
+        def forward(ctx, E, batch, ckpt_every):
+            E = E.contiguous()
+            psi0 = batch.save_state()
+            d = torch.zeros_like(E)
+            a = torch.zeros_like(E)
+            batch.propagate(E, d, a)
+            batch.load_state(psi0)
+            ctx.batch = batch
+            ctx.ckpt_every = ckpt_every
+            ctx.save_for_backward(E)
+            return d, a
+
+        @staticmethod
+        def backward(ctx, gd, ga):
+            (E,) = ctx.saved_tensors
+            gd = torch.zeros_like(E) if gd is None else gd.contiguous()
+            ga = torch.zeros_like(E) if ga is None else ga.contiguous()
+            gE = ctx.batch.adjoint(E, gd, ga, ckpt_every=ctx.ckpt_every)
+            return gE, None, None
+
+    return TDSEPropagate
+
+
+_autograd_fn = None
+
+
+def tdse_propagate_autograd(E, batch, ckpt_every=256):
+    """Differentiable propagation: returns (d, a); gradients flow to E (see TDSEPropagate)."""
+    global _autograd_fn
+    if _autograd_fn is None:
+        _autograd_fn = _make_autograd()
+    return _autograd_fn.apply(E, batch, ckpt_every)

@@ -415,3 +415,69 @@ def test_numerov_split_fp64_matches_oracle(env):
 def test_numerov_split_mixed_matches_oracle(env):
     tdse, oracle = env
     assert _numerov_case(tdse, oracle, tdse.TDSE_MIXED) < MIXED_SERIES
+
+
+# ------------------------------------------------------------------------------- adjoint
+
+def test_adjoint_matches_oracle_and_finite_differences(env):
+    """dL/dE from the adjoint kernel against the oracle's exact discrete adjoint, on a ragged batch
+    with checkpoint intervals that do not divide the lengths and groups sharing CTAs; then a
+    harmonic-window loss through torch autograd against central differences of the forward kernel."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    rng = np.random.default_rng(31)
+    n = 35
+    N, dx, dt, a = 384, 0.2, 0.05, 1.19
+    nt = rng.integers(150, 300, n)
+    nt[4] = 0
+    rows = [inputs.sin2_pulse(int(k), dt, rng.uniform(0.04, 0.09), 0.057, 1.0, rng.uniform(0, 6)) for k in nt]
+    offs = np.concatenate([[0], np.cumsum(nt + 1)])
+    dev = torch.device("cuda", 0)
+    Et = _device_rows(rows, offs, dev)
+    gd = torch.from_numpy(rng.standard_normal(int(offs[-1]))).to(dev)
+    ga = torch.from_numpy(rng.standard_normal(int(offs[-1]))).to(dev)
+    b = tdse.Batch([N] * n, dx, a, nt, dt, row_offsets=offs, absorber=(20.0, 0.125))
+    b.set_launch(3, 1, 0, 1)
+    b.ground_state(**GS_KW)
+    psi0, _, _ = oracle.ground_state(N, dx, a, **GS_KW)
+    m = oracle.mask(N, dx, 20.0, 0.125)
+    for kc in (37, 256):
+        gE = b.adjoint(Et, gd, ga, ckpt_every=kc).cpu().numpy()
+        torch.cuda.synchronize()
+        gdh, gah = gd.cpu().numpy(), ga.cpu().numpy()
+        for i in range(n):
+            sl = slice(offs[i], offs[i + 1])
+            ref = oracle.adjoint(psi0, rows[i], dx, dt, a, gdh[sl], gah[sl], mask_values=m)
+            assert _rel(gE[sl], ref) < RTOL_SERIES, (kc, i)
+    # the batch state is untouched by the adjoint
+    assert float((b.get_psi(0) - torch.from_numpy(psi0).to(dev)).abs().max()) < 1e-12
+    b.close()
+
+    # autograd on a harmonic-window yield of one instance vs central differences
+    nt1 = 400
+    E1 = inputs.sin2_pulse(nt1, dt, 0.07, 0.057, 1.0, 0.4)
+    b1 = tdse.Batch([N], dx, a, [nt1], dt, absorber=(20.0, 0.125))
+    b1.ground_state(**GS_KW)
+    L = nt1 + 1
+    q = np.fft.fftfreq(L, dt) * 2 * np.pi / 0.057
+    win = torch.from_numpy(((np.abs(q) >= 3) & (np.abs(q) <= 7)).astype(np.float64)).to(dev)
+
+    def loss_of(Ev):
+        _, acc = tdse.tdse_propagate_autograd(Ev, b1, ckpt_every=64)
+        S = torch.abs(torch.fft.fft(acc)) ** 2 * dt * dt
+        return (S * win).sum()
+
+    Ev = torch.from_numpy(E1).to(dev).requires_grad_(True)
+    lv = loss_of(Ev)
+    lv.backward()
+    g = Ev.grad.detach().cpu().numpy()
+    for k in (10, 150, 399):
+        eps = 1e-6
+        Ep = torch.from_numpy(E1).to(dev)
+        Ep[k] += eps
+        Em = torch.from_numpy(E1).to(dev)
+        Em[k] -= eps
+        with torch.no_grad():
+            fd = (loss_of(Ep) - loss_of(Em)).item() / (2 * eps)
+        assert abs(fd - g[k]) < 1e-5 * (abs(fd) + 1e-6 * abs(lv.item())), (k, fd, g[k])
+    b1.close()
