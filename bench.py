@@ -38,6 +38,7 @@ if ROOT not in sys.path:
 METRIC = "1D-TDSE grid-point-steps/s (batched) & % pipe roofline; mixed vs FP64 at stated error"
 UNIT = "grid-point-steps/s"
 FLOPS_PER_POINT_STEP = 48.0          # algorithmic FULL_CN work per grid-point step (FMA = 2 flops)
+MIXED_FP64_FLOPS_PER_POINT_STEP = 10.0   # MIXED: the FP64 pivot recurrence per grid-point step
 FP64_FMA_PER_CLK_PER_SM = 2.0        # GB300 FP64 pipe: 2 FMA/clk/SM (1.2 TFLOP/s measured at 2.0 GHz)
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
@@ -52,6 +53,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["own", "reference"], default="own")
+    p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large"], default="volume",
+                   help="volume = the benchmark; the others measure the other workloads (one JSON line each)")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                   help="arithmetic of the measured path (the volume benchmark's line is fp64)")
     p.add_argument("--e2e-steps", type=int, default=2, help="chunks timed end to end through host buffers")
     p.add_argument("--cpu-baseline", type=int, default=1, help="time the oracle on the host cores (rank 0, N = 1)")
     p.add_argument("--cpu-instances", type=int, default=0, help="oracle sample size (0 = one per core, max 16)")
@@ -198,10 +203,12 @@ def own_arm(args):
     import oracle  # test infrastructure: used only for the CPU baseline and the spectral check
     oracle.build()
 
-    # weak scaling: rank r owns its own 64 x 128 slice of a (64 x 128 world)-point volume
+    from paper_2507_04115_gb300 import sharding
+    # weak scaling: rank r owns its own 64 x 128 block of a (64 x 128 world)-point volume
     full = inputs.gaussian_beam_volume(n_z=128 * world) if world > 1 else inputs.volume_batch()
-    n = min(args.instances, 8192)
-    sl = slice(rank * 8192, rank * 8192 + n)
+    blk = sharding.contiguous(8192 * world, world, rank)
+    n = min(args.instances, blk.stop - blk.start)
+    sl = slice(blk.start, blk.start + n)
     N, dx, dt = int(full.N[0]), float(full.dx[0]), full.dt
     Nt = int(full.n_steps[0]) if args.nt <= 0 else min(args.nt, int(full.n_steps[0]))
     omega, ncyc = float(full.omega[0]), float(full.n_cycles[0])
@@ -233,8 +240,9 @@ def own_arm(args):
         cpu_async = cpu_pool.map_async(_oracle_job, jobs, chunksize=1)
 
     offs = np.arange(n + 1, dtype=np.int64) * (S + 1)
+    main_prec = tdse.TDSE_MIXED if args.precision == "mixed" else tdse.TDSE_FP64
     batch = tdse.Batch([N] * n, dx, a_soft, [Nt] * n, dt, row_offsets=offs,
-                       absorber=(full.mask_width, full.mask_exponent), device=local_rank)
+                       absorber=(full.mask_width, full.mask_exponent), precision=main_prec, device=local_rank)
     if args.warps or args.ctas_per_sm or args.slice:
         batch.set_launch(args.warps, args.ctas_per_sm, args.slice)
     plan = batch.plan()
@@ -373,7 +381,7 @@ def own_arm(args):
     # mixed precision on the same workload: throughput over two chunks of the whole batch, and the
     # spectral error of the oracle sample propagated in full (one group, so it runs on one SM)
     mixed = None
-    if args.mixed_compare and world == 1:
+    if args.mixed_compare and world == 1 and main_prec == tdse.TDSE_FP64:
         batch.close()
         mb = tdse.Batch([N] * n, dx, a_soft, [Nt] * n, dt, row_offsets=offs,
                         absorber=(full.mask_width, full.mask_exponent), precision=tdse.TDSE_MIXED, device=local_rank)
@@ -415,28 +423,33 @@ def own_arm(args):
 
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     pts_per_launch = float(n) * N * (timed_steps / args.steps)
-    achieved = FLOPS_PER_POINT_STEP * pts_per_launch / avg_launch_s
+    # FP64 work per point-step: the whole step in FP64; in MIXED only the pivot recurrence of the
+    # elimination stays on the FP64 pipe (10 flops + the reciprocal)
+    fp64_flops = FLOPS_PER_POINT_STEP if main_prec == tdse.TDSE_FP64 else MIXED_FP64_FLOPS_PER_POINT_STEP
+    achieved = fp64_flops * pts_per_launch / avg_launch_s
     peak = FP64_FMA_PER_CLK_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6
-    tpp = kernel_traffic_per_point_step()
+    tpp = kernel_traffic_per_point_step() if main_prec == tdse.TDSE_FP64 else None
     pipes = tdse.tdse_probe_pipes(local_rank)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tpp * pts_per_launch) if tpp is not None else None,
-                "kernel": "k_propagate_full_cn<fp64>", "pipe": "fp64",
+                "kernel": "k_propagate_full_cn<%s>" % args.precision, "pipe": "fp64",
                 "peak_how": "2 FP64 FMA/clk/SM x 152 SMs x 2 flops x 2070 MHz (unit counts at max clock)",
                 "fp64_fma_measured_tflops": pipes["fp64_fma_tflops"],
-                "achieved_how": "48 flops per grid-point step x points x steps per launch / mean CUDA-event "
-                                "launch time"}
+                "achieved_how": "%g FP64 flops per grid-point step x points x steps per launch / mean CUDA-event "
+                                "launch time" % fp64_flops}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if main_prec == tdse.TDSE_FP64 else "f32 psi / f64 elimination and sums",
+           "data": "synthetic",
            "config": {"workload": "volume batch 64r x 128z = 8192 instances per GPU, N=4096 dx=0.15, dt=0.02, "
                                   "800 nm 10-cycle sin^2 Gaussian-beam fields, FP64 FULL_CN, cos^(1/8) mask",
                       "instances_per_gpu": n, "N": N, "dx": dx, "dt": dt, "Nt": Nt, "chunk_steps": S,
                       "step": "one tdse_propagate call advancing every instance by chunk_steps time steps",
                       "l2": "inputs larger than L2: psi %.0f MB + scratch %.0f MB per GPU" %
                             (plan["psi_bytes"] / 1e6, plan["scratch_bytes"] / 1e6),
-                      "precision": "fp64", "scheme": "full_cn", "segments": plan["segments"],
+                      "precision": args.precision, "scheme": "full_cn", "segments": plan["segments"],
                       "halo": plan["halo"], "warps_per_cta": plan["warps_per_cta"], "ctas": plan["ctas"],
                       "slice_steps": plan["slice_steps"],
                       "parallelism": "instances sharded over GPUs, no collective"},
@@ -500,10 +513,147 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------------------------------- other workloads
+
+def _line(metric, value, unit, args, workload, cfg, **extra):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+           "config": dict(workload=workload, **cfg)}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def _fit(softcore, wl_target, classes, dev_index):
+    return {c: softcore.fit_softening(wl_target, c[0], c[1], device=dev_index) for c in classes}
+
+
+def other_workload(args):
+    """Single atom, uneven batch, adjoint batch and large volume: measured for the record, one line each."""
+    import torch
+    from paper_2507_04115_gb300 import build, inputs, softcore, tdse
+    build.build()
+    tdse.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    prec = tdse.TDSE_MIXED if args.precision == "mixed" else tdse.TDSE_FP64
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) * 1e-3
+
+    if args.workload == "single":
+        wl = inputs.single_atom()
+        N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+        a = softcore.fit_softening(wl.target_energy, N, dx)
+        E = torch.from_numpy(wl.field_rows()[0]).to(dev)
+        Nt = E.numel() - 1
+        res = {}
+        for pname, pv in (("fp64", tdse.TDSE_FP64), ("mixed", tdse.TDSE_MIXED)):
+            b = tdse.Batch([N], dx, a, [Nt], dt, absorber=(wl.mask_width, wl.mask_exponent), precision=pv)
+            b.set_launch(16)
+            d, acc = torch.zeros_like(E), torch.zeros_like(E)
+            ts = []
+            for k in range(args.warmup + args.steps):
+                b.ground_state()
+                t = timed(lambda: b.propagate(E, d, acc))
+                if k >= args.warmup:
+                    ts.append(t)
+            res[pname] = float(N) * Nt / statistics.mean(ts)
+            b.close()
+        _line(METRIC, res["fp64"], UNIT, args, "single atom N=2000 dx=0.2 dt=0.05, 800 nm 4-cycle sin^2, 8818 steps",
+              dict(N=N, dx=dx, dt=dt, Nt=Nt, step="one whole propagation of the single instance"),
+              dtype="f64", mixed={"value": res["mixed"], "speedup_vs_fp64": res["mixed"] / res["fp64"]},
+              solves_per_s=res["fp64"] / (N * Nt),
+              note="one instance uses one lane of one warp per segment: the layout is built for batches")
+        return
+
+    if args.workload in ("uneven", "large"):
+        wl = inputs.uneven_batch() if args.workload == "uneven" else inputs.large_volume()
+        n = wl.n_inst
+        classes = sorted(set(zip(wl.N.tolist(), wl.dx.tolist())))
+        soft = _fit(softcore, wl.target_energy, classes, 0)
+        a = np.array([soft[(int(N_), float(d_))] for N_, d_ in zip(wl.N, wl.dx)])
+        Nt_max = int(wl.n_steps.max())
+        S = int(args.nt) if args.nt > 0 else 2000
+        chunks = [(c * S, (c + 1) * S) for c in range(args.warmup + args.steps)]
+        offs = np.arange(n + 1, dtype=np.int64) * (S + 1)
+        b = tdse.Batch(wl.N, wl.dx, a, wl.n_steps, wl.dt, row_offsets=offs,
+                       absorber=(wl.mask_width, wl.mask_exponent), precision=prec)
+        b.ground_state()
+        Ebuf = torch.zeros(int(offs[-1]), dtype=torch.float64, device=dev)
+        d, acc = torch.zeros_like(Ebuf), torch.zeros_like(Ebuf)
+        dh = torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory()
+        Tp = wl.n_cycles * 2 * np.pi / wl.omega
+        E0t, wt, Tpt, pht = (torch.as_tensor(v, dtype=torch.float64, device=dev) for v in (wl.E0, wl.omega, Tp, wl.phi))
+
+        def fill(s0):   # field chunk generated on the device (the full field of the large volume is 104 GB)
+            t = (torch.arange(s0, s0 + S + 1, dtype=torch.float64, device=dev) * wl.dt)[None, :]
+            env = torch.where(t <= Tpt[:, None], torch.sin(np.pi * t / Tpt[:, None]) ** 2, torch.zeros_like(t))
+            Ebuf.view(n, S + 1).copy_(E0t[:, None] * env * torch.cos(wt[:, None] * (t - 0.5 * Tpt[:, None]) + pht[:, None]))
+
+        pts_total, t_total = 0.0, 0.0
+        for k, (s0, s1) in enumerate(chunks):
+            fill(s0)
+            t = timed(lambda: b.propagate(Ebuf, d, acc, s0, s1, sample_base=s0))
+            if args.workload == "large":
+                dh.copy_(acc, non_blocking=True)          # a(t) streamed back per chunk
+            if k >= args.warmup:
+                pts_total += float(np.sum(wl.N.astype(np.float64) * np.clip(np.minimum(wl.n_steps, s1) - s0, 0, None)))
+                t_total += t
+        torch.cuda.synchronize(dev)
+        plan = b.plan()
+        b.close()
+        _line(METRIC, pts_total / t_total, UNIT, args, wl.name,
+              dict(instances=n, chunk_steps=S, steps_covered=chunks[-1][1], Nt_max=Nt_max, classes=len(classes),
+                   precision=args.precision, ctas=plan["ctas"], warps_per_cta=plan["warps_per_cta"]),
+              dtype="f64" if prec == tdse.TDSE_FP64 else "f32 psi / f64 elimination",
+              total_point_steps=wl.point_steps(),
+              note="chunks of the first steps_covered steps; field chunks synthesised on the device")
+        return
+
+    if args.workload == "adjoint":
+        wl = inputs.adjoint_batch()
+        n = wl.n_inst
+        N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+        Nt = int(wl.n_steps[0]) if args.nt <= 0 else args.nt
+        a = softcore.fit_softening(wl.target_energy, N, dx)
+        E = torch.empty((n, Nt + 1), dtype=torch.float64, device=dev)
+        inputs.sin2_pulse_batch(Nt, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
+        E = E.reshape(-1).contiguous()
+        b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent))
+        b.set_launch(16)
+        b.ground_state()
+        d, acc = torch.zeros_like(E), torch.zeros_like(E)
+        psi0 = b.save_state()
+        t_fwd = timed(lambda: b.propagate(E, d, acc))
+        b.load_state(psi0)
+        # loss = harmonic yield of q in [21, 31]: dL/da from the spectrum of every row
+        L = Nt + 1
+        q = np.fft.fftfreq(L, dt) * 2 * np.pi / float(wl.omega[0])
+        win = torch.from_numpy(((np.abs(q) >= 21) & (np.abs(q) <= 31)).astype(np.float64)).to(dev)
+        A = torch.fft.fft(acc.view(n, L), dim=1)
+        ga = (2 * dt * dt * torch.fft.ifft(A * win[None, :], dim=1).real * L).reshape(-1).contiguous()
+        gd = torch.zeros_like(E)
+        t_adj = timed(lambda: b.adjoint(E, gd, ga, ckpt_every=256))
+        pts = float(n) * N * Nt
+        b.close()
+        _line("1D-TDSE adjoint gradient, forward-equivalent grid-point-steps/s", pts / t_adj, UNIT, args, wl.name,
+              dict(instances=n, N=N, Nt=Nt, ckpt_every=256, loss="sum of dt^2|DFT(a)|^2 over harmonics 21-31"),
+              dtype="f64", forward_value=pts / t_fwd, adjoint_over_forward_time=t_adj / t_fwd)
+        return
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload != "volume":
+        other_workload(args)
     else:
         own_arm(args)
 

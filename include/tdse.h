@@ -186,7 +186,8 @@ typedef struct {
 tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);
 
 /* Override the launch configuration for later calls (0 keeps the default of each):
- * warps_per_cta in [1, 16] (default 8; also the largest number of segments per instance),
+ * warps_per_cta in [1, 16] (default 8 for FP64, 12 for MIXED FULL_CN, 16 for MIXED NUMEROV_SPLIT; also
+ * the largest number of segments per instance),
  * ctas_per_sm in [1, 32] (default 1; clamped to the occupancy limit), slice_steps >= 1 (default 16),
  * max_ctas >= 1 caps the persistent grid (default: no cap beyond SMs x ctas_per_sm and the number
  * of groups).  Synchronises the device; the scratch is reallocated. */

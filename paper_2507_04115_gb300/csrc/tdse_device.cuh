@@ -19,6 +19,16 @@ __device__ __forceinline__ double rcp_pos(double n)
     return fma(y, t, y);
 }
 
+// 1/n to ~2^-40 relative (one second-order Newton-Raphson step from the hardware seed,
+// y = y0 (1 + e), e = 1 - n y0, error e^2): for coefficients that are rounded to float right after.
+__device__ __forceinline__ double rcp_pos_2nd(double n)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(n));
+    const double e = fma(-n, y, 1.0);
+    return fma(y, e, y);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -30,5 +40,54 @@ __device__ __forceinline__ double warp_sum(double v)
 // be served from a stale L1 line.
 __device__ __forceinline__ double2 ld_cg(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ float2 ld_cg(const float2* p) { return __ldcg(p); }
+
+// ---- bulk asynchronous copies (TMA, cp.async.bulk) into shared memory, completed on an mbarrier ----
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Make mbarrier initialisation visible to the async proxy before any copy uses the barrier.
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// 1D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing
+// `bytes` of transaction count on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Wait until the barrier's phase with the given parity completes; gives up after `limit` polls and
+// returns false (the caller records the timeout instead of hanging).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Order this thread's generic-proxy accesses before later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 }  // namespace tdse

@@ -45,6 +45,19 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
     const int P = blockDim.x >> 5;
     Cx* __restrict__ psi_all = static_cast<Cx*>(psi_raw);
     Cx* __restrict__ sc = static_cast<Cx*>(scratch_raw) + ((int64_t)blockIdx.x * P + w) * rows * (2 * kLanes);
+    // MIXED: per-warp ring of bulk-copy slots after the reduction area (see the back substitution)
+    const int kRing = full_cn_ring_slots(P);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(red + P * 3 * kLanes) + w * kRing;
+    unsigned char* ring = reinterpret_cast<unsigned char*>(reinterpret_cast<uint64_t*>(red + P * 3 * kLanes) + P * kRing) +
+                          (size_t)w * kRing * kSlotBytes;
+    uint32_t rc = 0;            // ring slots consumed by this warp so far (slot and phase of the next)
+    bool timed_out = false;
+    if constexpr (kMixed) {
+        if (lane == 0)
+            for (int k = 0; k < kRing; ++k) mbar_init(bars + k, 1);
+        fence_mbar_init();
+        __syncthreads();
+    }
 
     for (;;) {
         if (w == 0) {
@@ -81,6 +94,7 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const double2* __restrict__ tab_ab2 = reinterpret_cast<const double2*>(tab + tab_ab(C));
         const double2* __restrict__ tab_xv2 = reinterpret_cast<const double2*>(tab + tab_xv(C));
         const double* __restrict__ tab_m = tab + tab_mk(C);
+        const float4* __restrict__ tab_f4 = reinterpret_cast<const float4*>(tab + tab_fx(C));
         const int jm_lo = mask_on ? C.jm_lo : 0;
         const int jm_hi = mask_on ? C.jm_hi : N - 1;
         const int64_t n_end = min(step_end, G.nt_max);
@@ -124,19 +138,26 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
             double cr = 0.0, ci = 0.0;
             R Dr = 0, Di = 0;
             {
+                // pointers advance by increments: no 64-bit index arithmetic inside the loop
                 const Cx* pj = ps + (int64_t)lo * kLanes + lane;
                 Cx pa = lo < hi ? ld_cg(pj) : mk(R(0), R(0));
                 Cx pb = lo + 1 < hi ? ld_cg(pj + kLanes) : mk(R(0), R(0));
+                const Cx* pnext = pj + 2 * kLanes;
+                const double2* tp = tab_ab2 + lo;
                 Cx* r = sc;
 #pragma unroll 2
                 for (int j = lo; j < hi; ++j) {
                     const Cx p = pa;
                     pa = pb;
-                    if (j + 2 < hi) pb = ld_cg(ps + (int64_t)(j + 2) * kLanes + lane);
-                    const double2 t = __ldg(tab_ab2 + j);
+                    if (j + 2 < hi) pb = ld_cg(pnext);
+                    pnext += kLanes;
+                    const double2 t = __ldg(tp);
+                    ++tp;
                     const double Qr = inv_beta + ci;
                     const double Qi = fma(t.y, Eb, t.x) - cr;
-                    const double inv = rcp_pos(fma(Qr, Qr, Qi * Qi));
+                    // MIXED: gamma is rounded to float right after, so a 2^-40 reciprocal suffices
+                    // (the recurrence damps an error by beta^2 per point; it stays ~1e-12)
+                    const double inv = kMixed ? rcp_pos_2nd(fma(Qr, Qr, Qi * Qi)) : rcp_pos(fma(Qr, Qr, Qi * Qi));
                     cr = Qi * inv;
                     ci = Qr * inv;
                     R gr, gi;
@@ -156,13 +177,99 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     r += 2 * kLanes;
                 }
             }
+            if constexpr (kMixed) fence_proxy_async();   // scratch and psi stores precede the bulk reads
             __syncthreads();   // every read of psi^n (own segment and halos) precedes any write of psi^{n+1}
 
             // Back substitution Y_j = D_j + gamma_j Y_{j+1} (Y = beta y), seeded with 0 at hi (exact at
             // the wall), then psi^{n+1}_j = m_j (2 Y_j / beta - psi^n_j) on the own segment.
             R Yr = 0, Yi = 0;
             ObsSums o{0.0, 0.0, 0.0};
-            {
+            if constexpr (kMixed) {
+                // Rows hi-1 .. s stream through a per-warp ring of shared-memory slots filled by bulk
+                // asynchronous copies: a slot holds kSlotRows consecutive rows (their float2 gamma|D
+                // scratch rows, 512 bytes each, then their float2 psi rows, 256 bytes each), brought in
+                // by two copies completed on the slot's mbarrier, kRing slots ahead of the arithmetic:
+                // the float back substitution is too short per row to hide HBM latency by itself.
+                // After a wait that gives up (a failed copy) the ring is drained with bounded waits and
+                // not used again: the instances are flagged and nothing can hang.
+                const int nrows = hi - s;
+                const int nblk = (nrows + kSlotRows - 1) / kSlotRows;
+                auto issue = [&](int b) {
+                    const int j_top = hi - 1 - b * kSlotRows;
+                    const int cnt = min(kSlotRows, nrows - b * kSlotRows);
+                    const int j_bot = j_top - cnt + 1;
+                    const uint32_t k = (rc + b) % kRing;
+                    unsigned char* dst = ring + k * kSlotBytes;
+                    mbar_arrive_expect_tx(bars + k, (uint32_t)cnt * 768u);
+                    bulk_g2s(dst, sc + (int64_t)(j_bot - lo) * (2 * kLanes), (uint32_t)cnt * 512u, bars + k);
+                    bulk_g2s(dst + kSlotRows * 512, ps + (int64_t)j_bot * kLanes, (uint32_t)cnt * 256u, bars + k);
+                };
+                int issued = 0;
+                if (!timed_out) {
+                    if (lane == 0)
+                        for (int b = 0; b < min(kRing, nblk); ++b) issue(b);
+                    issued = min(kRing, nblk);
+                }
+                __syncwarp();
+                R fn = 0, fx = 0, fv = 0;
+                int blk = 0;
+                for (int b = 0; b < nblk && !timed_out; ++b) {
+                    const uint32_t k = (rc + b) % kRing;
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + k, ((rc + b) / kRing) & 1u, 1u << 22));
+                    if (!ok) {
+                        timed_out = true;
+                        for (int b2 = b + 1; b2 < issued; ++b2)
+                            mbar_wait(bars + (rc + b2) % kRing, ((rc + b2) / kRing) & 1u, 1u << 22);
+                        break;
+                    }
+                    const unsigned char* slotp = ring + k * kSlotBytes;
+                    const int j_top = hi - 1 - b * kSlotRows;
+                    const int cnt = min(kSlotRows, nrows - b * kSlotRows);
+                    const int j_bot = j_top - cnt + 1;
+                    for (int j = j_top; j >= j_bot; --j) {
+                        const int rr = j - j_bot;
+                        const float2* srow = reinterpret_cast<const float2*>(slotp + rr * 512);
+                        const float2 g2 = srow[lane], d2 = srow[kLanes + lane];
+                        const float2 old = reinterpret_cast<const float2*>(slotp + kSlotRows * 512 + rr * 256)[lane];
+                        const R nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
+                        Yi = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
+                        Yr = nr;
+                        if (j < e) {
+                            const float4 fxv = __ldg(tab_f4 + j);   // (x, dV/dx, m) in float
+                            R xr = fma(two_over_beta, Yr, -old.x);
+                            R xi = fma(two_over_beta, Yi, -old.y);
+                            if (j < jm_lo || j > jm_hi) {
+                                xr *= fxv.z;
+                                xi *= fxv.z;
+                            }
+                            if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
+                            const R rho = fma(xr, xr, xi * xi);
+                            fn += rho;
+                            fx = fma(fxv.x, rho, fx);
+                            fv = fma(fxv.y, rho, fv);
+                            if (++blk == 8) {
+                                o.n += (double)fn;
+                                o.x += (double)fx;
+                                o.v += (double)fv;
+                                fn = fx = fv = 0;
+                                blk = 0;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (b + kRing < nblk) {
+                        if (lane == 0) {
+                            fence_proxy_async();
+                            issue(b + kRing);
+                        }
+                        issued = b + kRing + 1;
+                    }
+                }
+                o.n += (double)fn;
+                o.x += (double)fx;
+                o.v += (double)fv;
+                rc += (uint32_t)max(nblk, 0);
+            } else {
                 const Cx* r = sc + (int64_t)(hi - 1 - lo) * (2 * kLanes);
                 for (int j = hi - 1; j >= e; --j) {
                     const Cx g2 = r[lane];
@@ -172,22 +279,23 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     Yi = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
                     Yr = nr;
                 }
-                // own segment, with the scratch row and the old psi prefetched two points ahead
+                // own segment, with the scratch row and the old psi prefetched two points ahead;
+                // pointers step down by decrements
                 Cx ga = mk(R(0), R(0)), da = ga, gb = ga, db = ga, pa = ga, pb = ga;
+                Cx* pw = ps + (int64_t)(e - 1) * kLanes + lane;       // psi_j (store)
+                const Cx* pl = pw - 2 * kLanes;                        // psi_{j-2} (prefetch)
+                const double* tm = tab_m + (e - 1);
+                const double2* txv = tab_xv2 + (e - 1);
                 if (e - 1 >= s) {
                     ga = r[lane];
                     da = r[kLanes + lane];
-                    pa = ld_cg(ps + (int64_t)(e - 1) * kLanes + lane);
+                    pa = ld_cg(pw);
                 }
                 if (e - 2 >= s) {
                     gb = r[-2 * kLanes + lane];
                     db = r[-kLanes + lane];
-                    pb = ld_cg(ps + (int64_t)(e - 2) * kLanes + lane);
+                    pb = ld_cg(pw - kLanes);
                 }
-                // MIXED: |psi|^2 and its weighted sums run in float over blocks of 8 points, each
-                // block total is added to the double accumulators
-                R fn = 0, fx = 0, fv = 0;
-                int blk = 0;
 #pragma unroll 2
                 for (int j = e - 1; j >= s; --j) {
                     const Cx g2 = ga, d2 = da, old = pa;
@@ -197,8 +305,9 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     if (j - 2 >= s) {
                         gb = r[-4 * kLanes + lane];
                         db = r[-3 * kLanes + lane];
-                        pb = ld_cg(ps + (int64_t)(j - 2) * kLanes + lane);
+                        pb = ld_cg(pl);
                     }
+                    pl -= kLanes;
                     r -= 2 * kLanes;
                     const R nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
                     Yi = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
@@ -206,34 +315,19 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     R xr = fma(two_over_beta, Yr, -old.x);
                     R xi = fma(two_over_beta, Yi, -old.y);
                     if (j < jm_lo || j > jm_hi) {
-                        const R mm = (R)__ldg(tab_m + j);
+                        const R mm = __ldg(tm);
                         xr *= mm;
                         xi *= mm;
                     }
-                    if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
+                    --tm;
+                    if (active) *pw = mk(xr, xi);
+                    pw -= kLanes;
                     const R rho = fma(xr, xr, xi * xi);
-                    const double2 xv = __ldg(tab_xv2 + j);
-                    if constexpr (kMixed) {
-                        fn += rho;
-                        fx = fma((R)xv.x, rho, fx);
-                        fv = fma((R)xv.y, rho, fv);
-                        if (++blk == 8) {
-                            o.n += (double)fn;
-                            o.x += (double)fx;
-                            o.v += (double)fv;
-                            fn = fx = fv = 0;
-                            blk = 0;
-                        }
-                    } else {
-                        o.n += rho;
-                        o.x = fma(xv.x, rho, o.x);
-                        o.v = fma(xv.y, rho, o.v);
-                    }
-                }
-                if constexpr (kMixed) {
-                    o.n += (double)fn;
-                    o.x += (double)fx;
-                    o.v += (double)fv;
+                    const double2 xv = __ldg(txv);
+                    --txv;
+                    o.n += rho;
+                    o.x = fma(xv.x, rho, o.x);
+                    o.v = fma(xv.y, rho, o.v);
                 }
             }
             const ObsSums t = reduce_obs(o, red, P);   // its barrier also orders this step's psi writes
@@ -246,6 +340,8 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
             }
         }
+
+        if (timed_out) status[G.slot0 + lane] = 2;   // a bulk copy did not complete in time
 
         // release the group: its psi writes become visible before the next owner's claim
         __threadfence();
@@ -271,8 +367,15 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d_progress, 0, sizeof(int) * n_groups, st);
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)P * 3 * kLanes * sizeof(double);
+    const size_t smem = full_cn_smem_bytes(mixed, P);
     if (mixed) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            e = cudaFuncSetAttribute(k_propagate_full_cn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)full_cn_smem_max_bytes());
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
         k_propagate_full_cn<true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
             sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status);
@@ -287,7 +390,13 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
 int propagate_max_ctas_per_sm(int mixed, int P)
 {
     int n = 0;
-    const size_t smem = (size_t)P * 3 * kLanes * sizeof(double);
+    const size_t smem = full_cn_smem_bytes(mixed, P);
+    if (mixed &&
+        cudaFuncSetAttribute(k_propagate_full_cn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)full_cn_smem_max_bytes()) != cudaSuccess) {
+        cudaGetLastError();   // do not leave the failure for the next launch check
+        return 1;
+    }
     const cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<true>, P * kLanes, smem)
                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<false>, P * kLanes, smem);
     if (e != cudaSuccess) return 1;

@@ -18,6 +18,7 @@ constexpr int kMaxSegments = 16;    // warps per CTA at most (512 threads)
 //   nw[j], nl[j], nc[j]: NUMEROV_SPLIT factors of A = M2 + i dt/2 (-Delta2/2 + M2 V) (complex):
 //            W_j/12 = 1/(12 pivot_j), L_j = A_{j,j-1}/pivot_j, C_j = A_{j,j+1}/pivot_j
 //   nf[3j..3j+2] = the same three factors rounded to float2 (MIXED)
+//   fx[j]  = (x_j, dV_j, m_j, 0) rounded to float4 (MIXED observables and mask)
 struct ClassDesc {
     int64_t tab_off;      // offset (in doubles) of the class block in the table buffer
     int32_t N;
@@ -46,7 +47,8 @@ __host__ __device__ inline int64_t tab_nw(const ClassDesc& c) { return c.tab_off
 __host__ __device__ inline int64_t tab_nl(const ClassDesc& c) { return c.tab_off + 7 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_nc(const ClassDesc& c) { return c.tab_off + 9 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_nf(const ClassDesc& c) { return c.tab_off + 11 * (int64_t)c.N; }
-inline int64_t tab_doubles(int N) { return 14 * (int64_t)N; }
+__host__ __device__ inline int64_t tab_fx(const ClassDesc& c) { return c.tab_off + 14 * (int64_t)c.N; }
+inline int64_t tab_doubles(int N) { return 16 * (int64_t)N; }
 
 // ---- host-side planning rules shared by the allocating and the static entry points ----
 

@@ -70,6 +70,7 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const double2* __restrict__ tL = reinterpret_cast<const double2*>(tab + tab_nl(C));
         const double2* __restrict__ tC = reinterpret_cast<const double2*>(tab + tab_nc(C));
         const float2* __restrict__ tF = reinterpret_cast<const float2*>(tab + tab_nf(C));
+        const float4* __restrict__ tab_f4 = reinterpret_cast<const float4*>(tab + tab_fx(C));
         const int jm_lo = mask_on ? C.jm_lo : 0;
         const int jm_hi = mask_on ? C.jm_hi : N - 1;
         const int64_t n_end = min(step_end, G.nt_max);
@@ -161,12 +162,20 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 // phase rotation per point: exp(+i dt E_n dx) steps x_j down by dx
                 R wr_, wi_;
                 if constexpr (kMixed) {
-                    sincosf((float)(dt * En * dx), &wi_, &wr_);
+                    sincosf(d2f(dt * En * dx), &wi_, &wr_);
                 } else {
                     sincos(dt * En * dx, &wi_, &wr_);
                 }
-                const R mdtE = (R)(-dt * En);
-                const R x0r = (R)x0, dxr = (R)dx;
+                R mdtE, x0r, dxr;
+                if constexpr (kMixed) {
+                    mdtE = d2f(-dt * En);
+                    x0r = d2f(x0);
+                    dxr = d2f(dx);
+                } else {
+                    mdtE = -dt * En;
+                    x0r = x0;
+                    dxr = dx;
+                }
                 R phr = 1, phi = 0;
                 const int reseed = kMixed ? 8 : 64;
                 R fn = 0, fx = 0, fv = 0;
@@ -201,18 +210,19 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     const R qr = fma(phr, wr_, -phi * wi_);
                     phi = fma(phr, wi_, phi * wr_);
                     phr = qr;
-                    if (j < jm_lo || j > jm_hi) {
-                        const R mm = (R)__ldg(tab_m + j);
-                        xr *= mm;
-                        xi *= mm;
-                    }
-                    if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
-                    const R rho = fma(xr, xr, xi * xi);
-                    const double2 xv = __ldg(tab_xv2 + j);
                     if constexpr (kMixed) {
+                        // float copies of (x, dV/dx, m): no double->float conversion per point (on
+                        // GB300 a conversion costs an FP64 pipe slot)
+                        const float4 fxv = __ldg(tab_f4 + j);
+                        if (j < jm_lo || j > jm_hi) {
+                            xr *= fxv.z;
+                            xi *= fxv.z;
+                        }
+                        if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
+                        const R rho = fma(xr, xr, xi * xi);
                         fn += rho;
-                        fx = fma((R)xv.x, rho, fx);
-                        fv = fma((R)xv.y, rho, fv);
+                        fx = fma(fxv.x, rho, fx);
+                        fv = fma(fxv.y, rho, fv);
                         if (++blk == 8) {
                             o.n += (double)fn;
                             o.x += (double)fx;
@@ -221,6 +231,14 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                             blk = 0;
                         }
                     } else {
+                        if (j < jm_lo || j > jm_hi) {
+                            const R mm = __ldg(tab_m + j);
+                            xr *= mm;
+                            xi *= mm;
+                        }
+                        if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
+                        const R rho = fma(xr, xr, xi * xi);
+                        const double2 xv = __ldg(tab_xv2 + j);
                         o.n += rho;
                         o.x = fma(xv.x, rho, o.x);
                         o.v = fma(xv.y, rho, o.v);

@@ -7,6 +7,35 @@
 
 namespace tdse {
 
+// MIXED back substitution streams its rows through a per-warp ring of shared-memory slots, each
+// holding kSlotRows rows (512-byte float2 gamma|D scratch rows, then 256-byte float2 psi rows):
+// 4 slots per warp when they fit in 220 KB, at least 2.
+constexpr int kSlotRows = 8;
+constexpr int kSlotBytes = kSlotRows * 768;
+constexpr int kMaxRing = 4;
+
+__host__ __device__ inline int full_cn_ring_slots(int P)
+{
+    const long red = (long)P * 3 * 32 * 8;
+    const long r = (220L * 1024 - red) / ((long)P * (kSlotBytes + 8));
+    return r < 2 ? 2 : (r > kMaxRing ? kMaxRing : (int)r);
+}
+
+__host__ __device__ inline size_t full_cn_smem_bytes(int mixed, int P)
+{
+    size_t b = (size_t)P * 3 * 32 * sizeof(double);
+    if (mixed) b += (size_t)P * full_cn_ring_slots(P) * (sizeof(uint64_t) + kSlotBytes);
+    return b;
+}
+
+// Largest dynamic shared memory the MIXED kernel asks for (over 1..16 warps).
+inline size_t full_cn_smem_max_bytes()
+{
+    size_t m = 0;
+    for (int P = 1; P <= 16; ++P) m = full_cn_smem_bytes(1, P) > m ? full_cn_smem_bytes(1, P) : m;
+    return m;
+}
+
 
 // Storage and arithmetic types per precision: FP64 keeps everything in double; MIXED keeps psi,
 // the solve's right-hand side and back substitution, and the pointwise update in float, while the
@@ -24,23 +53,24 @@ template <> struct Prec<true> {
 __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
 __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 
-// double -> float on the integer pipe for values well inside float's normal range: on GB300 a
-// hardware conversion costs as much as an FP64 multiply-add.  The 52-bit mantissa is rounded to 23
-// bits to nearest (ties away from zero; a carry into the exponent is the correct result), so the
-// rounding is unbiased -- truncation would perturb every step's elimination coefficients in the
-// same direction and the error would grow linearly with the number of steps.  Values outside the
-// range (including 0) take the hardware conversion.
+// double -> float on the integer pipe: on GB300 a hardware conversion costs as much as an FP64
+// multiply-add.  The 52-bit mantissa is rounded to 23 bits to nearest (ties away from zero; a carry
+// into the exponent is the correct result), so the rounding is unbiased -- truncation would perturb
+// every step's elimination coefficients in the same direction and the error would grow linearly
+// with the number of steps.  Magnitudes below float's normal range flush to a signed zero and
+// magnitudes above it saturate to float's largest finite value: the coefficients converted here
+// satisfy |gamma| <= beta < 1 and |gamma| >= beta/|q|, far inside the range.  No FP64 instruction.
 __device__ __forceinline__ float d2f(double x)
 {
     const int hi = __double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
     const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
-    if (e - 897u < 253u) {
-        const unsigned bits = ((unsigned)hi & 0x80000000u) | ((e - 896u) << 23) | (((unsigned)hi & 0xfffffu) << 3) |
-                              (lo >> 29);
-        return __uint_as_float(bits + ((lo >> 28) & 1u));
-    }
-    return __double2float_rn(x);
+    unsigned bits = sign | ((e - 896u) << 23) | (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    bits += (lo >> 28) & 1u;
+    bits = e < 897u ? sign : bits;
+    bits = e > 1149u ? (sign | 0x7f7fffffu) : bits;
+    return __uint_as_float(bits);
 }
 
 struct ObsSums {

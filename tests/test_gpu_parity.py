@@ -481,3 +481,80 @@ def test_adjoint_matches_oracle_and_finite_differences(env):
             fd = (loss_of(Ep) - loss_of(Em)).item() / (2 * eps)
         assert abs(fd - g[k]) < 1e-5 * (abs(fd) + 1e-6 * abs(lv.item())), (k, fd, g[k])
     b1.close()
+
+
+# ------------------------------------------------------------------------------- uneven batches, graphs
+
+def test_uneven_batch_like_the_uneven_workload(env):
+    """A scaled-down uneven batch (the uneven workload's distribution: several N and dx, pulse lengths
+    and wavelengths per instance) in one persistent launch; sampled instances against the oracle."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    rng = np.random.default_rng(41)
+    n = 96
+    Ns = np.array([256, 512, 768, 1024])
+    N = rng.choice(Ns, n)
+    dx = rng.choice(np.array([0.15, 0.2]), n)
+    soft = np.where(dx == 0.15, 1.19, 1.2)
+    dt = 0.02
+    lam = rng.choice(np.array([800.0, 1030.0, 1800.0]), n)
+    w = np.array([inputs.omega_from_wavelength_nm(l) for l in lam])
+    nt = rng.integers(100, 700, n)
+    rows = [inputs.sin2_pulse(int(nt[i]), dt, rng.uniform(0.03, 0.09), w[i], 0.5, 0.0) for i in range(n)]
+    offs = np.concatenate([[0], np.cumsum(nt + 1)])
+    dev = torch.device("cuda", 0)
+    Et = _device_rows(rows, offs, dev)
+    b = tdse.Batch(N, dx, soft, nt, dt, row_offsets=offs, absorber=(10.0, 0.125))
+    b.ground_state(**GS_KW)
+    d = torch.zeros_like(Et)
+    acc = torch.zeros_like(Et)
+    b.propagate(Et, d, acc)
+    torch.cuda.synchronize()
+    assert b.check() == -1
+    dh, ah = d.cpu().numpy(), acc.cpu().numpy()
+    for i in inputs.subsample(n, 12, 5):
+        psi0, _, _ = oracle.ground_state(int(N[i]), dx[i], soft[i], **GS_KW)
+        m = oracle.mask(int(N[i]), dx[i], 10.0, 0.125)
+        _, d_o, a_o = oracle.propagate(psi0, rows[i], dx[i], dt, soft[i], mask_values=m)
+        sl = slice(offs[i], offs[i + 1])
+        assert _rel(dh[sl], d_o) < RTOL_SERIES, i
+        assert _rel(ah[sl], a_o) < RTOL_SERIES, i
+    b.close()
+
+
+def test_chunked_propagation_replays_from_a_cuda_graph(env):
+    """State restore plus a sequence of chunk calls captured once in a CUDA graph and replayed gives the
+    same outputs as the eager calls (the calls launch kernels and memsets only: no host sync, no
+    allocation)."""
+    tdse, _ = env
+    from paper_2507_04115_gb300 import inputs
+    n, N, dx, a, dt, nt = 40, 512, 0.2, 1.19, 0.05, 240
+    rows = [inputs.sin2_pulse(nt, dt, 0.05 + 0.0005 * i, 0.057, 1.0, 0.0) for i in range(n)]
+    offs = np.arange(n + 1) * (nt + 1)
+    dev = torch.device("cuda", 0)
+    Et = _device_rows(rows, offs, dev)
+    b = tdse.Batch([N] * n, dx, a, [nt] * n, dt, absorber=(20.0, 0.125))
+    b.ground_state(**GS_KW)
+    psi0 = b.save_state()
+    d_ref, a_ref = torch.zeros_like(Et), torch.zeros_like(Et)
+    for s0 in range(0, nt, 60):
+        b.propagate(Et, d_ref, a_ref, s0, s0 + 60)
+    torch.cuda.synchronize()
+    d_g, a_g = torch.zeros_like(Et), torch.zeros_like(Et)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        b.load_state(psi0, stream=s)          # warm the code path once outside the capture
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            b.load_state(psi0, stream=s)
+            for s0 in range(0, nt, 60):
+                b.propagate(Et, d_g, a_g, s0, s0 + 60, stream=s)
+    for _ in range(2):
+        d_g.zero_()
+        a_g.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(d_g, d_ref) and torch.equal(a_g, a_ref)
+    b.close()
