@@ -64,6 +64,9 @@ def parse_args():
     p.add_argument("--warps", type=int, default=0, help="override warps per CTA (segments per instance)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="override CTAs per SM of the persistent grid")
     p.add_argument("--slice", type=int, default=0, help="override time steps per scheduling slice")
+    p.add_argument("--autotune", type=int, default=1,
+                   help="pick warps/CTAs per SM/slice with tdse_autotune before timing (untimed; 0 = planner default)")
+    p.add_argument("--tune-steps", type=int, default=256, help="time steps per autotuner probe")
     p.add_argument("--instances", type=int, default=8192, help="instances per GPU (smaller = profiling case)")
     p.add_argument("--nt", type=int, default=0, help="propagate only the first nt steps (0 = whole pulse)")
     p.add_argument("--mixed-compare", type=int, default=1,
@@ -271,6 +274,16 @@ def own_arm(args):
     dc = [torch.zeros(n * (S + 1), dtype=torch.float64, device=dev) for _ in chunks]
     ac = [torch.zeros(n * (S + 1), dtype=torch.float64, device=dev) for _ in chunks]
 
+    tune = None
+    if args.autotune and not (args.warps or args.ctas_per_sm or args.slice):
+        s0, s1 = chunks[0]
+        trials = batch.autotune(Ec[0], dc[0], ac[0], s0, min(s1, s0 + args.tune_steps), sample_base=s0, stream=stream)
+        plan = batch.plan()
+        tune = dict(probe_steps=min(s1, s0 + args.tune_steps) - s0, trials=len(trials),
+                    best_ms=min(t["ms"] for t in trials), default_ms=next(
+                        (t["ms"] for t in trials if (t["warps_per_cta"], t["ctas_per_sm"], t["slice_steps"]) ==
+                         (8 if main_prec == tdse.TDSE_FP64 else 12, 1, 16)), None))
+
     for c in range(args.warmup):
         s0, s1 = chunks[c]
         batch.propagate(Ec[c], dc[c], ac[c], s0, s1, sample_base=s0, stream=stream)
@@ -386,6 +399,13 @@ def own_arm(args):
         mb = tdse.Batch([N] * n, dx, a_soft, [Nt] * n, dt, row_offsets=offs,
                         absorber=(full.mask_width, full.mask_exponent), precision=tdse.TDSE_MIXED, device=local_rank)
         mb.ground_state()
+        m_tune = None
+        if args.autotune:
+            s0, s1 = chunks[0]
+            mt = mb.autotune(Ec[0], dc[0], ac[0], s0, min(s1, s0 + args.tune_steps), sample_base=s0, stream=stream)
+            mp = mb.plan()
+            m_tune = dict(warps_per_cta=mp["warps_per_cta"], ctas=mp["ctas"], slice_steps=mp["slice_steps"],
+                          trials=len(mt))
         n_m = min(2, n_chunks)
         mb.propagate(Ec[0], dc[0], ac[0], chunks[0][0], chunks[0][1], sample_base=chunks[0][0], stream=stream)
         torch.cuda.synchronize(dev)
@@ -399,7 +419,7 @@ def own_arm(args):
         torch.cuda.synchronize(dev)
         m_ms = e0_.elapsed_time(e1_)
         m_val = float(n) * N * sum(chunks[c][1] - chunks[c][0] for c in range(1, 1 + n_m)) / (m_ms * 1e-3)
-        mixed = {"value": m_val, "unit": UNIT, "speedup_vs_fp64": m_val / value, "steps": n_m,
+        mixed = {"value": m_val, "unit": UNIT, "speedup_vs_fp64": m_val / value, "steps": n_m, "launch": m_tune,
                  "dtype": "psi f32, elimination recurrence and observable sums f64"}
         mb.close()
         if cpu_async is not None:
@@ -451,7 +471,7 @@ def own_arm(args):
                             (plan["psi_bytes"] / 1e6, plan["scratch_bytes"] / 1e6),
                       "precision": args.precision, "scheme": "full_cn", "segments": plan["segments"],
                       "halo": plan["halo"], "warps_per_cta": plan["warps_per_cta"], "ctas": plan["ctas"],
-                      "slice_steps": plan["slice_steps"],
+                      "slice_steps": plan["slice_steps"], "autotune": tune,
                       "parallelism": "instances sharded over GPUs, no collective"},
            "solves_per_s": value / (N * Nt),
            "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clk,
@@ -552,11 +572,14 @@ def other_workload(args):
         a = softcore.fit_softening(wl.target_energy, N, dx)
         E = torch.from_numpy(wl.field_rows()[0]).to(dev)
         Nt = E.numel() - 1
-        res = {}
+        res, shapes = {}, {}
         for pname, pv in (("fp64", tdse.TDSE_FP64), ("mixed", tdse.TDSE_MIXED)):
             b = tdse.Batch([N], dx, a, [Nt], dt, absorber=(wl.mask_width, wl.mask_exponent), precision=pv)
-            b.set_launch(16)
             d, acc = torch.zeros_like(E), torch.zeros_like(E)
+            b.ground_state()
+            if args.autotune:
+                b.autotune(E, d, acc, 0, min(Nt, 512))
+            shapes[pname] = dict((k, b.plan()[k]) for k in ("lanes_per_instance", "warps_per_cta", "segments", "halo"))
             ts = []
             for k in range(args.warmup + args.steps):
                 b.ground_state()
@@ -566,10 +589,10 @@ def other_workload(args):
             res[pname] = float(N) * Nt / statistics.mean(ts)
             b.close()
         _line(METRIC, res["fp64"], UNIT, args, "single atom N=2000 dx=0.2 dt=0.05, 800 nm 4-cycle sin^2, 8818 steps",
-              dict(N=N, dx=dx, dt=dt, Nt=Nt, step="one whole propagation of the single instance"),
+              dict(N=N, dx=dx, dt=dt, Nt=Nt, step="one whole propagation of the single instance", layout=shapes),
               dtype="f64", mixed={"value": res["mixed"], "speedup_vs_fp64": res["mixed"] / res["fp64"]},
               solves_per_s=res["fp64"] / (N * Nt),
-              note="one instance uses one lane of one warp per segment: the layout is built for batches")
+              note="the instance spans the lanes of one CTA's warps (lane-split layout, one SM)")
         return
 
     if args.workload in ("uneven", "large"):
@@ -596,6 +619,13 @@ def other_workload(args):
             env = torch.where(t <= Tpt[:, None], torch.sin(np.pi * t / Tpt[:, None]) ** 2, torch.zeros_like(t))
             Ebuf.view(n, S + 1).copy_(E0t[:, None] * env * torch.cos(wt[:, None] * (t - 0.5 * Tpt[:, None]) + pht[:, None]))
 
+        tuned = None
+        if args.autotune and not (args.warps or args.ctas_per_sm or args.slice):
+            fill(0)
+            tr = b.autotune(Ebuf, d, acc, 0, min(S, args.tune_steps), sample_base=0)
+            tuned = len(tr)
+        elif args.warps or args.ctas_per_sm or args.slice:
+            b.set_launch(args.warps, args.ctas_per_sm, args.slice)
         pts_total, t_total = 0.0, 0.0
         for k, (s0, s1) in enumerate(chunks):
             fill(s0)
@@ -610,7 +640,8 @@ def other_workload(args):
         b.close()
         _line(METRIC, pts_total / t_total, UNIT, args, wl.name,
               dict(instances=n, chunk_steps=S, steps_covered=chunks[-1][1], Nt_max=Nt_max, classes=len(classes),
-                   precision=args.precision, ctas=plan["ctas"], warps_per_cta=plan["warps_per_cta"]),
+                   precision=args.precision, ctas=plan["ctas"], warps_per_cta=plan["warps_per_cta"],
+                   slice_steps=plan["slice_steps"], autotune_trials=tuned),
               dtype="f64" if prec == tdse.TDSE_FP64 else "f32 psi / f64 elimination",
               total_point_steps=wl.point_steps(),
               note="chunks of the first steps_covered steps; field chunks synthesised on the device")
@@ -626,9 +657,10 @@ def other_workload(args):
         inputs.sin2_pulse_batch(Nt, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
         E = E.reshape(-1).contiguous()
         b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent))
-        b.set_launch(16)
         b.ground_state()
         d, acc = torch.zeros_like(E), torch.zeros_like(E)
+        if args.autotune:
+            b.autotune(E, d, acc, 0, min(Nt, args.tune_steps))
         psi0 = b.save_state()
         t_fwd = timed(lambda: b.propagate(E, d, acc))
         b.load_state(psi0)
@@ -641,9 +673,11 @@ def other_workload(args):
         gd = torch.zeros_like(E)
         t_adj = timed(lambda: b.adjoint(E, gd, ga, ckpt_every=256))
         pts = float(n) * N * Nt
+        layout = dict((k, b.plan()[k]) for k in ("lanes_per_instance", "warps_per_cta", "segments", "halo", "ctas"))
         b.close()
         _line("1D-TDSE adjoint gradient, forward-equivalent grid-point-steps/s", pts / t_adj, UNIT, args, wl.name,
-              dict(instances=n, N=N, Nt=Nt, ckpt_every=256, loss="sum of dt^2|DFT(a)|^2 over harmonics 21-31"),
+              dict(instances=n, N=N, Nt=Nt, ckpt_every=256, loss="sum of dt^2|DFT(a)|^2 over harmonics 21-31",
+                   layout=layout),
               dtype="f64", forward_value=pts / t_fwd, adjoint_over_forward_time=t_adj / t_fwd)
         return
 

@@ -168,10 +168,12 @@ tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream)
 tdse_status tdse_spectrum(const double* a_dev, const int64_t* offsets_host, int64_t n_rows, double dt,
                           int64_t k_begin, int64_t k_end, double* S_dev, void* stream);
 
-/* Plan chosen for the batch (for benchmarks and tests): number of 32-instance groups, grid
- * segments per instance (largest over the classes), halo length in points (largest), warps per
- * CTA, CTAs of the persistent propagation grid, time steps per scheduling slice, and the bytes of
- * the propagation scratch and of the wavefunctions. */
+/* Plan chosen for the batch (for benchmarks and tests): number of instance groups, warps
+ * carrying grid segments per instance (largest over the classes), halo length in points (largest),
+ * warps per CTA, CTAs of the persistent propagation grid, time steps per scheduling slice, the
+ * bytes of the propagation scratch and of the wavefunctions, and the lanes per instance of the
+ * layout (largest over the classes; see tdse_set_layout).  An instance is cut into
+ * segments x lanes_per_instance segments. */
 typedef struct {
     int64_t n_groups;
     int32_t segments;
@@ -181,9 +183,23 @@ typedef struct {
     int32_t slice_steps;
     int64_t scratch_bytes;
     int64_t psi_bytes;
+    int32_t lanes_per_instance;
 } tdse_plan_info;
 
 tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);
+
+/* How instances map onto the lanes of a warp.  The paper has no counterpart (its solver is serial
+ * per MPI rank); this is the GPU layout choice.  With lanes_per_instance L = 1 a warp carries 32
+ * instances, one per lane, each cut into as many segments as the CTA has warps.  With L in
+ * {2, 4, 8, 16, 32} a warp carries 32/L instances and each spans L lanes, so every instance is cut
+ * into L times more segments: more halo work per point, but 32/L-instance groups occupy L times
+ * more SMs, which pays when the batch is too small to fill the GPU.  L = 0 (the default at
+ * creation) picks L from a cost model of the batch: FP64 warp instructions of a step per group
+ * against the number of SMs.  NUMEROV_SPLIT batches and classes whose halo cannot be truncated
+ * (dt/(4 dx^2) >= 0.85) always use L = 1.  The wavefunction state is discarded (call before
+ * tdse_ground_state, tdse_set_psi or tdse_copy_state); synchronises the device and reallocates.
+ * Returns TDSE_ERR_ARG for L outside {0, 1, 2, 4, 8, 16, 32}. */
+tdse_status tdse_set_layout(tdse_batch* batch, int32_t lanes_per_instance);
 
 /* Override the launch configuration for later calls (0 keeps the default of each):
  * warps_per_cta in [1, 16] (default 8 for FP64, 12 for MIXED FULL_CN, 16 for MIXED NUMEROV_SPLIT; also
@@ -193,6 +209,34 @@ tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);
  * of groups).  Synchronises the device; the scratch is reallocated. */
 tdse_status tdse_set_launch(tdse_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
                             int32_t max_ctas);
+
+/* Launch-shape autotuner.  The paper runs one solver per MPI rank and has no counterpart; this
+ * picks, by timing, the shape tdse_set_launch sets: warps per CTA (also the number of segments
+ * each instance's tridiagonal solve is split into, i.e. the depth of the parallel split), CTAs per
+ * SM and the scheduling slice.  It times tdse_propagate over steps [step_begin, step_end) of the
+ * given field rows (same arguments as tdse_propagate) for each candidate, every trial starting
+ * from the batch's current state, which is restored afterwards: a coordinate search over
+ * warps {4, 6, 8, 12, 16} x CTAs per SM {1, 2} at a 16-step slice, then slices {8, 32, 64} at the
+ * best pair; shapes that the occupancy clamp makes identical are timed once.  The fastest shape
+ * stays set on the batch.
+ *   d_dev, a_dev    rows over the probed steps are scratch: overwritten by the probes
+ *   repeats         timed runs per candidate in [1, 100] (the minimum counts); the first
+ *                   candidate also gets one untimed run
+ *   trials_host     optional (max_trials may be 0): receives up to max_trials trials in the order
+ *                   run; *n_trials_host (may be NULL) receives how many were run.
+ * Synchronous: it synchronises the stream and the device (tdse_set_launch), allocates a device
+ * copy of the state for the duration of the call, and must not be called during stream capture. */
+typedef struct {
+    int32_t warps_per_cta;
+    int32_t ctas_per_sm;
+    int32_t slice_steps;
+    int32_t ctas;   /* resulting persistent grid size */
+    float ms;       /* fastest of the timed runs, milliseconds */
+} tdse_tune_trial;
+
+tdse_status tdse_autotune(tdse_batch* batch, const double* E_dev, double* d_dev, double* a_dev, int64_t sample_base,
+                          int64_t step_begin, int64_t step_end, int32_t repeats, tdse_tune_trial* trials_host,
+                          int32_t max_trials, int32_t* n_trials_host, void* stream);
 
 /* FULL_CN FP64 propagation that allocates nothing, for callers that cannot call cudaMalloc: code
  * embedded in a host application that owns the whole device-memory budget (a pre-sized pool it
@@ -222,8 +266,11 @@ tdse_status tdse_propagate_static(const tdse_instance* inst_host, int64_t n_inst
  * copy/GEMM peak table): FP64 and FP32 fused multiply-add throughput with every SM busy, FP64 warp
  * instructions per second with one active lane per warp (the cost is per warp instruction), FP64
  * throughput with 1, 2 and 4 warps per SM (one FP64 unit per SM sub-partition), and
- * double->float->double conversion pairs per second.  Runs a few short bounded launches on
- * `device` (synchronous; allocates a small buffer). */
+ * double->float->double conversion pairs per second, and the cost of a reciprocal seed in FP64 FMA
+ * slots: the hardware double approximation (rcp.approx.ftz.f64, the seed the kernels use) and a
+ * float-based alternative (float approximation of the truncated value, integer exponent shifts),
+ * each measured as the extra time of a loop that adds one seed per FMA over the FMA-only loop.
+ * Runs a few short bounded launches on `device` (synchronous; allocates a small buffer). */
 typedef struct {
     double fp64_fma_tflops;
     double fp64_warp_instr_per_s;
@@ -233,6 +280,8 @@ typedef struct {
     double cvt_pairs_per_s;
     int32_t sm_count;
     double sm_clock_mhz;
+    double rcp_f64_approx_fma_slots;
+    double rcp_seed_fma_slots;
 } tdse_pipe_rates;
 
 tdse_status tdse_probe_pipes(int device, tdse_pipe_rates* out_host);

@@ -13,9 +13,14 @@
 // The solve with A_n reuses the forward kernel's segmented, halo-truncated Thomas sweep.
 //
 // Memory: the forward states are recomputed from checkpoints every K steps; within a checkpoint
-// interval the pre-mask states psi~ are kept on a per-CTA tape.  One CTA owns a group (32
-// instances) for the whole call: first a forward pass writing the checkpoints, then the intervals
-// from last to first (recompute the interval onto the tape, then sweep it backwards).
+// interval the pre-mask states psi~ are kept on a per-CTA tape.  One CTA owns a group for the whole
+// call: first a forward pass writing the checkpoints, then the intervals from last to first
+// (recompute the interval onto the tape, then sweep it backwards).
+//
+// Lane geometry (any group width I = 32/L, see GroupDesc): lane l of warp w holds instance l % I
+// and sweeps segment sigma = w L + l / I over rows r = 0 .. m + 2K - 1 at points sigma m - K + r;
+// rows outside the grid restart the recurrences at the walls, so every lane of a warp runs the
+// same trip counts; the own segment is rows K .. K + m - 1.
 #include "tdse_sched.cuh"
 
 namespace tdse {
@@ -23,66 +28,121 @@ namespace tdse {
 namespace {
 
 struct AdjGeom {
-    int N, s, e, lo, hi;
-    double beta, inv_beta, two_over_beta;
+    int N, I, i, q, base, nrows, K, m, s, e;
+    double inv_beta, two_over_beta;
+    __device__ __forceinline__ int64_t at(int j) const { return (int64_t)j * I + i; }
 };
 
-// One FULL_CN step on the work state ps (layout [N][32]); optionally stores the pre-mask state into
+__device__ __forceinline__ AdjGeom adj_geom(const GroupDesc& G, double beta)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    AdjGeom g;
+    g.N = G.N;
+    g.I = G.I;
+    const int L = kLanes / G.I;
+    g.i = lane & (G.I - 1);
+    g.q = lane / G.I;
+    g.K = G.K;
+    g.m = G.m;
+    const int sigma = w * L + g.q;
+    g.nrows = w < G.P ? G.m + 2 * G.K : 0;
+    g.base = sigma * G.m - G.K;
+    g.s = w < G.P ? min(G.N, sigma * G.m) : G.N;
+    g.e = w < G.P ? min(G.N, sigma * G.m + G.m) : G.N;
+    g.inv_beta = 1.0 / beta;
+    g.two_over_beta = 2.0 / beta;
+    return g;
+}
+
+// sum over the L lanes of an instance, then over the warps (warp 0 lanes q == 0 get the totals)
+__device__ __forceinline__ ObsSums adj_reduce(ObsSums o, const AdjGeom& g, double* red, int P)
+{
+    for (int off = g.I; off < kLanes; off <<= 1) {
+        o.n += __shfl_xor_sync(0xffffffffu, o.n, off);
+        o.x += __shfl_xor_sync(0xffffffffu, o.x, off);
+        o.v += __shfl_xor_sync(0xffffffffu, o.v, off);
+    }
+    return reduce_obs(o, red, P);
+}
+
+// Forward elimination of A y = v over the lane's sweep rows (v from `src`, a callable giving the
+// right-hand side at point j), writing (gamma, D) rows to the scratch.
+template <class Rhs>
+__device__ __forceinline__ void eliminate(const AdjGeom& g, double Eb, const double2* __restrict__ tab_ab2,
+                                          double2* __restrict__ sc, Rhs rhs)
+{
+    const int lane = threadIdx.x & 31;
+    double cr = 0.0, ci = 0.0, Dr = 0.0, Di = 0.0;
+    double2* r = sc;
+    for (int rr = 0; rr < g.nrows; ++rr) {
+        const int j = g.base + rr;
+        const bool in = (unsigned)j < (unsigned)g.N;
+        const int jc = min(max(j, 0), g.N - 1);
+        const double2 v = in ? rhs(jc) : make_double2(0.0, 0.0);
+        const double2 t = __ldg(tab_ab2 + jc);
+        const double Qr = g.inv_beta + ci;
+        const double Qi = fma(t.y, Eb, t.x) - cr;
+        const double inv = rcp_pos(fma(Qr, Qr, Qi * Qi));
+        cr = in ? Qi * inv : 0.0;
+        ci = in ? Qr * inv : 0.0;
+        const double ur = v.x - Di;
+        const double ui = v.y + Dr;
+        Dr = in ? fma(cr, ui, ci * ur) : 0.0;
+        Di = in ? fma(ci, ui, -cr * ur) : 0.0;
+        r[lane] = make_double2(cr, ci);
+        r[kLanes + lane] = make_double2(Dr, Di);
+        r += 2 * kLanes;
+    }
+}
+
+// Back substitution over rows nrows-1 .. K, calling own(j, Yr, Yi) on the own segment's points.
+template <class Own>
+__device__ __forceinline__ void substitute(const AdjGeom& g, const double2* __restrict__ sc, Own own)
+{
+    const int lane = threadIdx.x & 31;
+    double Yr = 0.0, Yi = 0.0;
+    const double2* r = sc + (int64_t)(g.nrows - 1) * (2 * kLanes);
+    for (int rr = g.nrows - 1; rr >= g.K; --rr) {
+        const int j = g.base + rr;
+        const double2 g2 = r[lane];
+        const double2 d2 = r[kLanes + lane];
+        r -= 2 * kLanes;
+        const double nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
+        const double ni = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
+        Yr = j < g.N ? nr : 0.0;
+        Yi = j < g.N ? ni : 0.0;
+        if (rr < g.K + g.m && j < g.N) own(j, Yr, Yi);
+    }
+}
+
+// One FULL_CN step on the work state ps (layout [N][I]); optionally stores the pre-mask state into
 // tape.  Ends with a barrier so that the next step sees every segment's writes.
 __device__ __forceinline__ void fwd_step(double2* __restrict__ ps, const AdjGeom& g, double Eb,
                                          const double2* __restrict__ tab_ab2, const double* __restrict__ tab_m,
                                          int jm_lo, int jm_hi, double2* __restrict__ sc, bool active,
                                          double2* __restrict__ tape)
 {
-    const int lane = threadIdx.x & 31;
-    double cr = 0.0, ci = 0.0, Dr = 0.0, Di = 0.0;
-    double2* r = sc;
-    for (int j = g.lo; j < g.hi; ++j) {
-        const double2 p = ld_cg(ps + (int64_t)j * kLanes + lane);
-        const double2 t = __ldg(tab_ab2 + j);
-        const double Qr = g.inv_beta + ci;
-        const double Qi = fma(t.y, Eb, t.x) - cr;
-        const double inv = rcp_pos(fma(Qr, Qr, Qi * Qi));
-        cr = Qi * inv;
-        ci = Qr * inv;
-        const double ur = p.x - Di;
-        const double ui = p.y + Dr;
-        Dr = fma(cr, ui, ci * ur);
-        Di = fma(ci, ui, -cr * ur);
-        r[lane] = make_double2(cr, ci);
-        r[kLanes + lane] = make_double2(Dr, Di);
-        r += 2 * kLanes;
-    }
+    eliminate(g, Eb, tab_ab2, sc, [&](int j) { return ld_cg(ps + g.at(j)); });
     __syncthreads();
-    double Yr = 0.0, Yi = 0.0;
-    const double2* q = sc + (int64_t)(g.hi - 1 - g.lo) * (2 * kLanes);
-    for (int j = g.hi - 1; j >= g.s; --j) {
-        const double2 g2 = q[lane];
-        const double2 d2 = q[kLanes + lane];
-        q -= 2 * kLanes;
-        const double nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
-        Yi = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
-        Yr = nr;
-        if (j < g.e) {
-            double2* pp = ps + (int64_t)j * kLanes + lane;
-            const double2 old = *pp;
-            double xr = fma(g.two_over_beta, Yr, -old.x);
-            double xi = fma(g.two_over_beta, Yi, -old.y);
-            if (tape) tape[(int64_t)j * kLanes + lane] = active ? make_double2(xr, xi) : old;
-            if (j < jm_lo || j > jm_hi) {
-                const double mm = __ldg(tab_m + j);
-                xr *= mm;
-                xi *= mm;
-            }
-            if (active) *pp = make_double2(xr, xi);
+    substitute(g, sc, [&](int j, double Yr, double Yi) {
+        double2* pp = ps + g.at(j);
+        const double2 old = *pp;
+        double xr = fma(g.two_over_beta, Yr, -old.x);
+        double xi = fma(g.two_over_beta, Yi, -old.y);
+        if (tape) tape[g.at(j)] = active ? make_double2(xr, xi) : old;
+        if (j < jm_lo || j > jm_hi) {
+            const double mm = __ldg(tab_m + j);
+            xr *= mm;
+            xi *= mm;
         }
-    }
+        if (active) *pp = make_double2(xr, xi);
+    });
     __syncthreads();
 }
 
-__device__ __forceinline__ void copy_state(double2* __restrict__ dst, const double2* __restrict__ src, int N)
+__device__ __forceinline__ void copy_state(double2* __restrict__ dst, const double2* __restrict__ src, int64_t n)
 {
-    for (int64_t k = threadIdx.x; k < (int64_t)N * kLanes; k += blockDim.x) dst[k] = ld_cg(src + k);
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) dst[k] = ld_cg(src + k);
 }
 
 }  // namespace
@@ -121,21 +181,14 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
 
         const GroupDesc G = groups[gi];
         const ClassDesc C = cls[G.cls];
-        const int N = G.N, Pg = G.P, K = G.K, m = G.m;
-        const int64_t slot = G.slot0 + lane;
+        const AdjGeom geo = adj_geom(G, C.beta);
+        const int N = G.N, L = kLanes / G.I;
+        const int64_t slot = G.slot0 + geo.i;
         const int64_t nt = slot_nt[slot];
         const int64_t row = slot_row[slot];
         const int64_t nt_max = G.nt_max;
+        const int64_t state = (int64_t)N * G.I;   // elements of one state of the group
         const double dx = C.dx, h = 2.0 * C.beta * dx * dx;   // h = dt/2 = 2 beta dx^2
-        AdjGeom geo;
-        geo.N = N;
-        geo.s = w < Pg ? min(N, w * m) : N;
-        geo.e = w < Pg ? min(N, geo.s + m) : N;
-        geo.lo = w < Pg ? max(0, geo.s - K) : N;
-        geo.hi = w < Pg ? min(N, geo.e + K) : N;
-        geo.beta = C.beta;
-        geo.inv_beta = 1.0 / C.beta;
-        geo.two_over_beta = 2.0 / C.beta;
         const double2* __restrict__ tab_ab2 = reinterpret_cast<const double2*>(tab + tab_ab(C));
         const double2* __restrict__ tab_xv2 = reinterpret_cast<const double2*>(tab + tab_xv(C));
         const double* __restrict__ tab_m = tab + tab_mk(C);
@@ -145,31 +198,31 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
         double2* __restrict__ ck = ckpt_all + ckpt_off[gi];
         const int64_t n_int = (nt_max + kc - 1) / kc;   // checkpoint intervals
 
-        // gE rows start at zero
+        // gE rows start at zero (the L lanes of an instance and the warps share the row)
         if (nt >= 0)
-            for (int64_t n = w; n <= nt; n += P) gE[row + n] = 0.0;
+            for (int64_t n = w * L + geo.q; n <= nt; n += P * L) gE[row + n] = 0.0;
 
         // forward pass from psi^0, checkpoint every kc steps
-        copy_state(work, psi0_all + G.psi_off, N);
-        copy_state(ck, psi0_all + G.psi_off, N);
+        copy_state(work, psi0_all + G.psi_off, state);
+        copy_state(ck, psi0_all + G.psi_off, state);
         __syncthreads();
         for (int64_t n = 0; n < nt_max; ++n) {
             const bool active = n < nt;
             const double Eb = active ? 0.5 * (E[row + n] + E[row + n + 1]) : 0.0;
             fwd_step(work, geo, Eb, tab_ab2, tab_m, jm_lo, jm_hi, sc, active, nullptr);
             if ((n + 1) % kc == 0 && n + 1 < nt_max) {
-                copy_state(ck + ((n + 1) / kc) * (int64_t)N * kLanes, work, N);
+                copy_state(ck + ((n + 1) / kc) * state, work, state);
                 __syncthreads();
             }
         }
-        for (int64_t k = threadIdx.x; k < (int64_t)N * kLanes; k += blockDim.x) lam[k] = make_double2(0.0, 0.0);
+        for (int64_t k = threadIdx.x; k < state; k += blockDim.x) lam[k] = make_double2(0.0, 0.0);
         __syncthreads();
 
         // backward over the checkpoint intervals, last first
         for (int64_t c = n_int - 1; c >= 0; --c) {
             const int64_t na = c * kc, nb = min(nt_max, na + kc);
-            const double2* __restrict__ cks = ck + c * (int64_t)N * kLanes;
-            copy_state(work, cks, N);
+            const double2* __restrict__ cks = ck + c * state;
+            copy_state(work, cks, state);
             __syncthreads();
             for (int64_t n = na; n < nb; ++n) {
                 const bool active = n < nt;
@@ -177,7 +230,7 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
                 fwd_step(work, geo, Eb, tab_ab2, tab_m, jm_lo, jm_hi, sc, active, tape + (n - na) * (int64_t)n_max * kLanes);
             }
             for (int64_t n = nb - 1; n >= na; --n) {
-                const bool term = (n + 1 == nt);     // this lane's last sample: lambda starts here
+                const bool term = (n + 1 == nt);     // this instance's last sample: lambda starts here
                 const bool active = n < nt;
                 const double2* __restrict__ pt1 = tape + (n - na) * (int64_t)n_max * kLanes;              // psi~^{n+1}
                 const double2* __restrict__ pt0 = n > na ? tape + (n - na - 1) * (int64_t)n_max * kLanes : nullptr;
@@ -194,79 +247,50 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
                 double norm_term = 0.0;
                 if (term) {
                     for (int j = geo.s; j < geo.e; ++j) {
-                        const double2 q = ld_cg(pt1 + (int64_t)j * kLanes + lane);
+                        const double2 q = ld_cg(pt1 + geo.at(j));
                         const double mm = (j < jm_lo || j > jm_hi) ? __ldg(tab_m + j) : 1.0;
                         const double2 xv = __ldg(tab_xv2 + j);
                         const double pr = mm * q.x, pi = mm * q.y;
                         const double wgt = 2.0 * dx * fma(gd1, xv.x, ga1 * (xv.y + En1));
-                        lam[(int64_t)j * kLanes + lane] = make_double2(wgt * pr, wgt * pi);
+                        lam[geo.at(j)] = make_double2(wgt * pr, wgt * pi);
                         norm_term = fma(pr, pr, fma(pi, pi, norm_term));
                     }
                 }
                 __syncthreads();
-                // B: solve A_n y = conj(M lambda^{n+1}) -- forward elimination over the halo range
+                // B: solve A_n y = conj(M lambda^{n+1}) -- forward elimination over the sweep rows
                 const double Eb = 0.5 * (En + En1);
-                {
-                    double cr = 0.0, ci = 0.0, Dr = 0.0, Di = 0.0;
-                    double2* r = sc;
-                    for (int j = geo.lo; j < geo.hi; ++j) {
-                        const double2 lv = ld_cg(lam + (int64_t)j * kLanes + lane);
-                        const double mm = (j < jm_lo || j > jm_hi) ? __ldg(tab_m + j) : 1.0;
-                        const double vr = mm * lv.x, vi = -mm * lv.y;   // conj(M lambda)
-                        const double2 t = __ldg(tab_ab2 + j);
-                        const double Qr = geo.inv_beta + ci;
-                        const double Qi = fma(t.y, Eb, t.x) - cr;
-                        const double inv = rcp_pos(fma(Qr, Qr, Qi * Qi));
-                        cr = Qi * inv;
-                        ci = Qr * inv;
-                        const double ur = vr - Di;
-                        const double ui = vi + Dr;
-                        Dr = fma(cr, ui, ci * ur);
-                        Di = fma(ci, ui, -cr * ur);
-                        r[lane] = make_double2(cr, ci);
-                        r[kLanes + lane] = make_double2(Dr, Di);
-                        r += 2 * kLanes;
-                    }
-                }
+                eliminate(geo, Eb, tab_ab2, sc, [&](int j) {
+                    const double2 lv = ld_cg(lam + geo.at(j));
+                    const double mm = (j < jm_lo || j > jm_hi) ? __ldg(tab_m + j) : 1.0;
+                    return make_double2(mm * lv.x, -mm * lv.y);   // conj(M lambda)
+                });
                 __syncthreads();
                 // C: back substitution, mu = conj(y), lambda^n = 2 mu - M lambda^{n+1} + g^n, field gradient
                 ObsSums o{0.0, 0.0, norm_term};
-                {
-                    double Yr = 0.0, Yi = 0.0;
-                    const double2* q = sc + (int64_t)(geo.hi - 1 - geo.lo) * (2 * kLanes);
-                    for (int j = geo.hi - 1; j >= geo.s; --j) {
-                        const double2 g2 = q[lane];
-                        const double2 d2 = q[kLanes + lane];
-                        q -= 2 * kLanes;
-                        const double nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
-                        Yi = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
-                        Yr = nr;
-                        if (j < geo.e) {
-                            const double mur = Yr * geo.inv_beta, mui = -Yi * geo.inv_beta;
-                            const double mm = (j < jm_lo || j > jm_hi) ? __ldg(tab_m + j) : 1.0;
-                            double2* lp = lam + (int64_t)j * kLanes + lane;
-                            const double2 lv = *lp;
-                            const double vr = mm * lv.x, vi = mm * lv.y;
-                            double2 p0;
-                            if (pt0) {
-                                const double2 q0 = ld_cg(pt0 + (int64_t)j * kLanes + lane);
-                                p0 = make_double2(mm * q0.x, mm * q0.y);
-                            } else {
-                                p0 = ld_cg(cks + (int64_t)j * kLanes + lane);
-                            }
-                            const double2 p1 = ld_cg(pt1 + (int64_t)j * kLanes + lane);
-                            const double2 xv = __ldg(tab_xv2 + j);
-                            const double wgt = 2.0 * dx * fma(gdn, xv.x, gan * (xv.y + En));
-                            if (active)
-                                *lp = make_double2(fma(2.0, mur, fma(wgt, p0.x, -vr)), fma(2.0, mui, fma(wgt, p0.y, -vi)));
-                            const double sr = p0.x + p1.x, si = p0.y + p1.y;
-                            o.n = fma(xv.x, fma(mur, si, -mui * sr), o.n);
-                            o.x = fma(p0.x, p0.x, fma(p0.y, p0.y, o.x));
-                        }
+                substitute(geo, sc, [&](int j, double Yr, double Yi) {
+                    const double mur = Yr * geo.inv_beta, mui = -Yi * geo.inv_beta;
+                    const double mm = (j < jm_lo || j > jm_hi) ? __ldg(tab_m + j) : 1.0;
+                    double2* lp = lam + geo.at(j);
+                    const double2 lv = *lp;
+                    const double vr = mm * lv.x, vi = mm * lv.y;
+                    double2 p0;
+                    if (pt0) {
+                        const double2 q0 = ld_cg(pt0 + geo.at(j));
+                        p0 = make_double2(mm * q0.x, mm * q0.y);
+                    } else {
+                        p0 = ld_cg(cks + geo.at(j));
                     }
-                }
-                const ObsSums t = reduce_obs(o, red, P);
-                if (w == 0) {
+                    const double2 p1 = ld_cg(pt1 + geo.at(j));
+                    const double2 xv = __ldg(tab_xv2 + j);
+                    const double wgt = 2.0 * dx * fma(gdn, xv.x, gan * (xv.y + En));
+                    if (active)
+                        *lp = make_double2(fma(2.0, mur, fma(wgt, p0.x, -vr)), fma(2.0, mui, fma(wgt, p0.y, -vi)));
+                    const double sr = p0.x + p1.x, si = p0.y + p1.y;
+                    o.n = fma(xv.x, fma(mur, si, -mui * sr), o.n);
+                    o.x = fma(p0.x, p0.x, fma(p0.y, p0.y, o.x));
+                });
+                const ObsSums t = adj_reduce(o, geo, red, P);
+                if (w == 0 && geo.q == 0) {
                     if (term) gE[row + nt] += ga1 * dx * t.v;
                     if (active) {
                         const double gbar = h * t.n;
@@ -283,12 +307,12 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
             double s0 = 0.0;
             if (nt == 0) {
                 for (int j = geo.s; j < geo.e; ++j) {
-                    const double2 p = ld_cg(psi0_all + G.psi_off + (int64_t)j * kLanes + lane);
+                    const double2 p = ld_cg(psi0_all + G.psi_off + geo.at(j));
                     s0 = fma(p.x, p.x, fma(p.y, p.y, s0));
                 }
             }
-            const ObsSums t = reduce_obs(ObsSums{s0, 0.0, 0.0}, red, P);
-            if (w == 0 && nt == 0) gE[row] = ga[row] * dx * t.n;
+            const ObsSums t = adj_reduce(ObsSums{s0, 0.0, 0.0}, geo, red, P);
+            if (w == 0 && geo.q == 0 && nt == 0) gE[row] = ga[row] * dx * t.n;
             __syncthreads();
         }
 

@@ -88,8 +88,10 @@ struct tdse_batch {
     std::vector<int> inst_class;
     std::vector<int64_t> slot_of_inst;
     std::vector<GroupDesc> groups;
-    std::vector<int> class_P, class_K;
+    std::vector<int> class_P, class_K, class_L;
+    std::vector<int64_t> slot_group;   // group of every slot
     int64_t n_slots = 0;
+    int lanes_request = 0;             // tdse_set_layout's lanes per instance (0 = cost model)
     // launch configuration of the persistent propagation kernel
     int warps_override = 0, ctas_per_sm_override = 0, slice_override = 0, max_ctas_override = 0;
     int warps = 8, ctas = 0, rows = 0, slice = 16;
@@ -213,23 +215,160 @@ double numerov_factors(const ClassDesc& C, double dt, std::vector<double>& nw, s
     return rho;
 }
 
+int default_warps(const tdse_batch* b)
+{
+    // measured on the 8192 x 4096 volume batch: FP64 is FP64-pipe bound with two warps per
+    // sub-partition; the MIXED kernels need more warps to cover latency
+    if (b->precision == TDSE_MIXED) return b->scheme == TDSE_NUMEROV_SPLIT ? 16 : 12;
+    return 8;
+}
+
+// Lanes per instance for the lane-split layout, from a cost model of one time step: a group's
+// step costs ceil(P/4) x (27 m + 36 K) FP64 warp instructions on its busiest SM sub-partition
+// (27 per own point: forward elimination 16, back substitution and update 11; 36 per halo point:
+// 2K forward rows and K back-substitution rows), with m = N / (P L).  The step time is the larger
+// of (total work / SMs) and the longest single group (one group runs on one SM).  L = 1 keeps
+// 32 instances per warp; a larger L is taken only when it is clearly faster, i.e. when the
+// batch has too few groups to occupy the SMs.  NUMEROV_SPLIT and classes without a usable halo
+// keep L = 1.
+int model_lanes(const tdse_batch* b, const std::vector<int64_t>& class_count)
+{
+    if (b->scheme == TDSE_NUMEROV_SPLIT) return 1;
+    const int warps = b->warps_override > 0 ? b->warps_override : default_warps(b);
+    double best_t = 0.0;
+    int best_L = 1;
+    for (int L = 1; L <= kLanes; L *= 2) {
+        double work = 0.0, longest = 0.0;
+        for (size_t c = 0; c < b->classes.size(); ++c) {
+            const ClassDesc& C = b->classes[c];
+            const int K = halo_for_beta(C.beta);
+            const int Lc = K == 0 ? 1 : L;
+            const int P = Lc == 1 ? class_segments(C.N, K, warps) : std::max(1, std::min(warps, C.N / Lc));
+            const int m = group_segment_length(C.N, P, Lc);
+            const double cost = std::ceil(P / 4.0) * (27.0 * m + 36.0 * (P * Lc > 1 ? K : 0));
+            const double groups = std::ceil((double)class_count[c] * Lc / kLanes);
+            work += groups * cost;
+            longest = std::max(longest, cost);
+        }
+        const double t = std::max(work / std::max(1, b->sm_count), longest);
+        if (L == 1 || t < 0.9 * best_t) {
+            best_t = t;
+            best_L = L;
+        }
+    }
+    return best_L;
+}
+
+// Slots and groups: instances ordered by class, then by decreasing Nt (long groups first), cut
+// into groups of I = 32/L; (re)allocates everything sized by the grouping.  The state is lost.
+tdse_status build_groups(tdse_batch* b)
+{
+    const int n_cls = (int)b->classes.size();
+    const int64_t n_inst = b->n_inst;
+    std::vector<int64_t> class_count(n_cls, 0);
+    for (int64_t i = 0; i < n_inst; ++i) ++class_count[b->inst_class[i]];
+    const int L = b->lanes_request > 0 ? (b->scheme == TDSE_NUMEROV_SPLIT ? 1 : b->lanes_request)
+                                       : model_lanes(b, class_count);
+    b->class_L.assign(n_cls, 1);
+    for (int c = 0; c < n_cls; ++c) b->class_L[c] = halo_for_beta(b->classes[c].beta) == 0 ? 1 : L;
+
+    std::vector<int64_t> order(n_inst);
+    for (int64_t i = 0; i < n_inst; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t p, int64_t q) {
+        if (b->inst_class[p] != b->inst_class[q]) return b->inst_class[p] < b->inst_class[q];
+        return b->n_steps[p] > b->n_steps[q];
+    });
+    b->groups.clear();
+    b->slot_group.clear();
+    b->slot_of_inst.assign(n_inst, -1);
+    std::vector<int64_t> slot_row, slot_nt, slot_valid;
+    int64_t psi_elems = 0;
+    for (int64_t k = 0; k < n_inst;) {
+        const int c = b->inst_class[order[k]];
+        const int I = kLanes / b->class_L[c];
+        while (k < n_inst && b->inst_class[order[k]] == c) {
+            GroupDesc G{};
+            G.cls = c;
+            G.N = b->classes[c].N;
+            G.I = I;
+            G.slot0 = (int64_t)slot_row.size();
+            G.psi_off = psi_elems;
+            psi_elems += (int64_t)G.N * I;
+            G.nt_max = 0;
+            for (int q = 0; q < I; ++q) {
+                b->slot_group.push_back((int64_t)b->groups.size());
+                if (k < n_inst && b->inst_class[order[k]] == c) {
+                    const int64_t i = order[k++];
+                    b->slot_of_inst[i] = (int64_t)slot_row.size();
+                    slot_row.push_back(b->row_off[i]);
+                    slot_nt.push_back(b->n_steps[i]);
+                    slot_valid.push_back(1);
+                    G.nt_max = std::max(G.nt_max, b->n_steps[i]);
+                } else {
+                    slot_row.push_back(0);
+                    slot_nt.push_back(-1);
+                    slot_valid.push_back(0);
+                }
+            }
+            b->groups.push_back(G);
+        }
+    }
+    b->n_slots = (int64_t)slot_row.size();
+    b->psi_elems = psi_elems;
+    b->initialized = false;
+
+    cudaFree(b->d_groups);
+    cudaFree(b->d_slot_row);
+    cudaFree(b->d_slot_nt);
+    cudaFree(b->d_slot_valid);
+    cudaFree(b->d_psi);
+    cudaFree(b->d_status);
+    cudaFree(b->d_busy);
+    cudaFree(b->d_progress);
+    b->d_groups = nullptr;
+    b->d_slot_row = b->d_slot_nt = b->d_slot_valid = nullptr;
+    b->d_psi = nullptr;
+    b->d_status = b->d_busy = b->d_progress = nullptr;
+    // adjoint buffers are sized by the grouping: dropped, reallocated by the next tdse_adjoint
+    cudaFree(b->d_lam);
+    cudaFree(b->d_ckpt);
+    cudaFree(b->d_ckpt_off);
+    cudaFree(b->d_work);
+    cudaFree(b->d_tape);
+    b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
+    b->d_ckpt_off = nullptr;
+    b->adj_kc = 0;
+    TDSE_CUDA(dev_alloc(&b->d_groups, b->groups.size()), "cudaMalloc(groups)");
+    TDSE_CUDA(dev_alloc(&b->d_slot_row, (size_t)b->n_slots), "cudaMalloc(slots)");
+    TDSE_CUDA(dev_alloc(&b->d_slot_nt, (size_t)b->n_slots), "cudaMalloc(slots)");
+    TDSE_CUDA(dev_alloc(&b->d_slot_valid, (size_t)b->n_slots), "cudaMalloc(slots)");
+    TDSE_CUDA(cudaMalloc(&b->d_psi, (size_t)std::max<int64_t>(psi_elems, 1) * b->cx_bytes()), "cudaMalloc(psi)");
+    TDSE_CUDA(dev_alloc(&b->d_status, (size_t)b->n_slots), "cudaMalloc(status)");
+    TDSE_CUDA(dev_alloc(&b->d_busy, b->groups.size()), "cudaMalloc(sched)");
+    TDSE_CUDA(dev_alloc(&b->d_progress, b->groups.size()), "cudaMalloc(sched)");
+    TDSE_CUDA(cudaMemcpy(b->d_slot_row, slot_row.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
+    TDSE_CUDA(cudaMemcpy(b->d_slot_nt, slot_nt.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
+    TDSE_CUDA(cudaMemcpy(b->d_slot_valid, slot_valid.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
+    TDSE_CUDA(cudaMemset(b->d_status, 0, sizeof(int) * b->n_slots), "cudaMemset(status)");
+    TDSE_CUDA(cudaMemset(b->d_psi, 0, b->cx_bytes() * (size_t)std::max<int64_t>(psi_elems, 1)), "cudaMemset(psi)");
+    return TDSE_OK;
+}
+
 // (Re)compute the launch configuration, the group descriptors and the scratch, and (re)allocate.
 tdse_status build_plan(tdse_batch* b)
 {
     const int n_cls = (int)b->classes.size();
-    // default warps per CTA (measured on the 8192 x 4096 volume batch): FP64 is FP64-pipe bound
-    // with two warps per sub-partition; the MIXED kernels need more warps to cover latency
-    int def_warps = 8;
-    if (b->precision == TDSE_MIXED) def_warps = b->scheme == TDSE_NUMEROV_SPLIT ? 16 : 12;
-    b->warps = b->warps_override > 0 ? b->warps_override : def_warps;
+    b->warps = b->warps_override > 0 ? b->warps_override : default_warps(b);
     b->slice = b->slice_override > 0 ? b->slice_override : 16;
     b->class_P.assign(n_cls, 1);
     b->class_K.assign(n_cls, 0);
     for (int c = 0; c < n_cls; ++c) {
         const ClassDesc& C = b->classes[c];
         int K = halo_for_beta(b->scheme == TDSE_NUMEROV_SPLIT ? C.rho : C.beta);
-        const int P = class_segments(C.N, K, b->warps);
-        if (P == 1) K = 0;
+        const int L = b->class_L[c];
+        // lane-split classes use every warp (short segments are the price of filling the GPU)
+        const int P = L == 1 ? class_segments(C.N, K, b->warps) : std::max(1, std::min(b->warps, C.N / L));
+        if (P == 1 && L == 1) K = 0;
         b->class_P[c] = P;
         b->class_K[c] = K;
     }
@@ -238,8 +377,10 @@ tdse_status build_plan(tdse_batch* b)
         const int P = b->class_P[G.cls], K = b->class_K[G.cls];
         G.P = P;
         G.K = K;
-        G.m = (G.N + P - 1) / P;
-        rows = std::max(rows, std::min(G.N, G.m + 2 * K));
+        G.m = group_segment_length(G.N, P, kLanes / G.I);
+        // a sweep covers its segment and a halo on each side (m + 2K rows; the 32-wide propagation
+        // clips it at the walls); a single exact segment covers the N points
+        rows = std::max(rows, P * (kLanes / G.I) == 1 ? G.N : G.m + 2 * K);
     }
     b->rows = rows;
     const int per_sm_max = propagate_max_ctas_per_sm(b->mixed(), b->warps);
@@ -259,6 +400,10 @@ tdse_status build_plan(tdse_batch* b)
 bool is_finite(double v) { return std::isfinite(v); }
 
 }  // namespace
+
+namespace tdse {
+int batch_device(const tdse_batch* b) { return b->device; }
+}  // namespace tdse
 
 extern "C" {
 
@@ -357,46 +502,6 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
             C.jm_hi = hi_j;   // empty plateau (lo > hi) masks every point
         }
     }
-    // slots: instances ordered by class, then by decreasing Nt (long groups first); groups of 32
-    std::vector<int64_t> order(n_inst);
-    for (int64_t i = 0; i < n_inst; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int64_t p, int64_t q) {
-        if (b->inst_class[p] != b->inst_class[q]) return b->inst_class[p] < b->inst_class[q];
-        return b->n_steps[p] > b->n_steps[q];
-    });
-    b->slot_of_inst.assign(n_inst, -1);
-    std::vector<int64_t> slot_row, slot_nt, slot_valid;
-    int64_t psi_elems = 0;
-    for (int64_t k = 0; k < n_inst;) {
-        const int c = b->inst_class[order[k]];
-        while (k < n_inst && b->inst_class[order[k]] == c) {
-            GroupDesc G{};
-            G.cls = c;
-            G.N = b->classes[c].N;
-            G.slot0 = (int64_t)slot_row.size();
-            G.psi_off = psi_elems;
-            psi_elems += (int64_t)G.N * kLanes;
-            G.nt_max = 0;
-            for (int lane = 0; lane < kLanes; ++lane) {
-                if (k < n_inst && b->inst_class[order[k]] == c) {
-                    const int64_t i = order[k++];
-                    b->slot_of_inst[i] = (int64_t)slot_row.size();
-                    slot_row.push_back(b->row_off[i]);
-                    slot_nt.push_back(b->n_steps[i]);
-                    slot_valid.push_back(1);
-                    G.nt_max = std::max(G.nt_max, b->n_steps[i]);
-                } else {
-                    slot_row.push_back(0);
-                    slot_nt.push_back(-1);
-                    slot_valid.push_back(0);
-                }
-            }
-            b->groups.push_back(G);
-        }
-    }
-    b->n_slots = (int64_t)slot_row.size();
-    b->psi_elems = psi_elems;
-
     // device allocations
     tdse_status st = TDSE_OK;
     auto bail = [&](tdse_status s) {
@@ -406,18 +511,10 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     };
     cudaError_t e;
     if ((e = dev_alloc(&b->d_cls, n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(classes)"));
-    if ((e = dev_alloc(&b->d_groups, b->groups.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(groups)"));
     if ((e = dev_alloc(&b->d_tab, (size_t)tab_total)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(tables)"));
-    if ((e = dev_alloc(&b->d_slot_row, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
-    if ((e = dev_alloc(&b->d_slot_nt, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
-    if ((e = dev_alloc(&b->d_slot_valid, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots)"));
-    if ((e = cudaMalloc(&b->d_psi, (size_t)std::max<int64_t>(psi_elems, 1) * b->cx_bytes())) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaMalloc(psi)"));
-    if ((e = dev_alloc(&b->d_status, (size_t)b->n_slots)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(status)"));
-    if ((e = dev_alloc(&b->d_busy, b->groups.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(sched)"));
-    if ((e = dev_alloc(&b->d_progress, b->groups.size())) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(sched)"));
     if ((e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    if ((st = build_groups(b)) != TDSE_OK) return bail(st);
     int64_t gs_total = 0;
     std::vector<int64_t> gs_off(n_cls);
     for (int c = 0; c < n_cls; ++c) {
@@ -429,12 +526,7 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     if ((e = dev_alloc(&b->d_gs_energy, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
     if ((e = dev_alloc(&b->d_gs_iters, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
     if ((e = cudaMemcpy(b->d_cls, b->classes.data(), sizeof(ClassDesc) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->d_slot_row, slot_row.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->d_slot_nt, slot_nt.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->d_slot_valid, slot_valid.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->d_gs_off, gs_off.data(), sizeof(int64_t) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(b->d_status, 0, sizeof(int) * b->n_slots)) != cudaSuccess ||
-        (e = cudaMemset(b->d_psi, 0, b->cx_bytes() * (size_t)std::max<int64_t>(psi_elems, 1))) != cudaSuccess)
+        (e = cudaMemcpy(b->d_gs_off, gs_off.data(), sizeof(int64_t) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemcpy(setup)"));
     if ((e = launch_build_tables(b->d_cls, n_cls, max_N, dt, b->mask_width, b->mask_exp, b->mask_on, b->d_tab, 0)) != cudaSuccess)
         return bail(cuda_fail(e, "build_tables launch"));
@@ -478,7 +570,23 @@ tdse_status tdse_plan(const tdse_batch* b, tdse_plan_info* info)
     info->slice_steps = b->slice;
     info->scratch_bytes = b->scratch_elems * (int64_t)b->cx_bytes();
     info->psi_bytes = b->psi_elems * (int64_t)b->cx_bytes();
+    info->lanes_per_instance = b->class_L.empty() ? 1 : *std::max_element(b->class_L.begin(), b->class_L.end());
     return TDSE_OK;
+}
+
+tdse_status tdse_set_layout(tdse_batch* b, int32_t lanes_per_instance)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_set_layout: NULL batch");
+    const int L = lanes_per_instance;
+    if (L < 0 || L > kLanes || (L & (L - 1)) != 0)
+        return fail(TDSE_ERR_ARG, "tdse_set_layout: lanes_per_instance must be 0, 1, 2, 4, 8, 16 or 32");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    TDSE_CUDA(cudaDeviceSynchronize(), "tdse_set_layout: synchronize");
+    b->lanes_request = L;
+    tdse_status st = build_groups(b);
+    if (st != TDSE_OK) return st;
+    return build_plan(b);
 }
 
 tdse_status tdse_set_launch(tdse_batch* b, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
@@ -567,14 +675,15 @@ tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, do
     return TDSE_OK;
 }
 
-static tdse_status locate(const tdse_batch* b, int64_t inst, int64_t* off, int* N, int* lane)
+static tdse_status locate(const tdse_batch* b, int64_t inst, int64_t* off, int* N, int* lane, int* I)
 {
     if (inst < 0 || inst >= b->n_inst) return fail(TDSE_ERR_ARG, "instance index out of range");
     const int64_t slot = b->slot_of_inst[inst];
-    const GroupDesc& G = b->groups[slot / kLanes];
+    const GroupDesc& G = b->groups[b->slot_group[slot]];
     *off = G.psi_off;
     *N = G.N;
-    *lane = (int)(slot % kLanes);
+    *lane = (int)(slot - G.slot0);
+    *I = G.I;
     return TDSE_OK;
 }
 
@@ -582,12 +691,12 @@ tdse_status tdse_get_psi(tdse_batch* b, int64_t inst, double* psi_dev, void* str
 {
     if (!b || !psi_dev) return fail(TDSE_ERR_ARG, "tdse_get_psi: NULL argument");
     int64_t off;
-    int N, lane;
-    tdse_status s = locate(b, inst, &off, &N, &lane);
+    int N, lane, I;
+    tdse_status s = locate(b, inst, &off, &N, &lane, &I);
     if (s != TDSE_OK) return s;
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
-    TDSE_CUDA(launch_get_psi(b->mixed(), b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "get_psi launch");
+    TDSE_CUDA(launch_get_psi(b->mixed(), b->d_psi, off, N, lane, I, psi_dev, (cudaStream_t)stream), "get_psi launch");
     return TDSE_OK;
 }
 
@@ -595,12 +704,12 @@ tdse_status tdse_set_psi(tdse_batch* b, int64_t inst, const double* psi_dev, voi
 {
     if (!b || !psi_dev) return fail(TDSE_ERR_ARG, "tdse_set_psi: NULL argument");
     int64_t off;
-    int N, lane;
-    tdse_status s = locate(b, inst, &off, &N, &lane);
+    int N, lane, I;
+    tdse_status s = locate(b, inst, &off, &N, &lane, &I);
     if (s != TDSE_OK) return s;
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
-    TDSE_CUDA(launch_set_psi(b->mixed(), b->d_psi, off, N, lane, psi_dev, (cudaStream_t)stream), "set_psi launch");
+    TDSE_CUDA(launch_set_psi(b->mixed(), b->d_psi, off, N, lane, I, psi_dev, (cudaStream_t)stream), "set_psi launch");
     b->initialized = true;
     return TDSE_OK;
 }
@@ -677,7 +786,7 @@ tdse_status tdse_adjoint(tdse_batch* b, const double* E_dev, const double* gd_de
         for (size_t g = 0; g < b->groups.size(); ++g) {
             off[g] = total;
             const int64_t n_int = (b->groups[g].nt_max + ckpt_every - 1) / ckpt_every;
-            total += (n_int + 1) * (int64_t)b->groups[g].N * kLanes;
+            total += (n_int + 1) * (int64_t)b->groups[g].N * b->groups[g].I;
         }
         const size_t cx = sizeof(double2);
         TDSE_CUDA(cudaMalloc(&b->d_lam, (size_t)std::max<int64_t>(b->psi_elems, 1) * cx), "cudaMalloc(adjoint lambda)");

@@ -27,6 +27,160 @@
 
 namespace tdse {
 
+// One scheduling slice of a lane-split group (G.I = 32/L instances, each over L lanes of every
+// warp; see GroupDesc).  Lane l of warp w holds instance i = l % I and sweeps segment
+// sigma = w L + l / I, i.e. sweep rows r = 0 .. m + 2K - 1 at points j = sigma m - K + r: every
+// lane of a warp runs the same trip counts whatever its segment.  Rows before the first wall
+// restart the forward coefficients at zero (the exact boundary condition of the Thomas sweep),
+// rows at or beyond the far wall restart the back substitution at zero; the own segment is rows
+// K .. K + m - 1.  Observables are summed over the L lanes of an instance by shuffles, then over the
+// warps.  No bulk copies on this path (it serves small batches, where the FP64 elimination is the
+// bound in both precisions); MIXED sums the observables in double directly.
+template <bool kMixed>
+__device__ __forceinline__ void split_slice(const GroupDesc& G, typename Prec<kMixed>::C* __restrict__ ps,
+                                            const double2* __restrict__ tab_ab2, const double2* __restrict__ tab_xv2,
+                                            const double* __restrict__ tab_m, double inv_beta,
+                                            typename Prec<kMixed>::R two_over_beta, double dx, int jm_lo, int jm_hi,
+                                            int64_t nt, int64_t row, int64_t slot, int64_t n0, int64_t n1,
+                                            bool initial, const double* __restrict__ E, double* __restrict__ d_out,
+                                            double* __restrict__ a_out, int64_t sample_base,
+                                            typename Prec<kMixed>::C* __restrict__ sc, double* red, int* status)
+{
+    using R = typename Prec<kMixed>::R;
+    using Cx = typename Prec<kMixed>::C;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int P = blockDim.x >> 5;
+    const int I = G.I, L = kLanes / G.I;
+    const int i = lane & (I - 1), q = lane / I;
+    const int N = G.N, K = G.K, m = G.m;
+    const int sigma = w * L + q;
+    const int nrows = w < G.P ? m + 2 * K : 0;   // warp-uniform
+    const int base = sigma * m - K;
+    const int s_own = min(N, sigma * m), e_own = min(N, sigma * m + m);
+    auto lane_sum = [&](ObsSums o) {
+        for (int off = I; off < kLanes; off <<= 1) {
+            o.n += __shfl_xor_sync(0xffffffffu, o.n, off);
+            o.x += __shfl_xor_sync(0xffffffffu, o.x, off);
+            o.v += __shfl_xor_sync(0xffffffffu, o.v, off);
+        }
+        return o;
+    };
+
+    if (initial) {
+        ObsSums o{0.0, 0.0, 0.0};
+        if (w < G.P)
+            for (int j = s_own; j < e_own; ++j) {
+                const Cx p = ld_cg(ps + (int64_t)j * I + i);
+                const double rho = fma((double)p.x, (double)p.x, (double)p.y * (double)p.y);
+                const double2 xv = __ldg(tab_xv2 + j);
+                o.n += rho;
+                o.x = fma(xv.x, rho, o.x);
+                o.v = fma(xv.y, rho, o.v);
+            }
+        const ObsSums t = reduce_obs(lane_sum(o), red, P);
+        if (w == 0 && q == 0 && nt >= 0) {
+            const double E0 = E[row - sample_base];
+            d_out[row - sample_base] = t.x * dx;
+            a_out[row - sample_base] = fma(E0, t.n, t.v) * dx;
+        }
+        __syncthreads();
+    }
+
+    for (int64_t n = n0; n < n1; ++n) {
+        const bool active = n < nt;
+        double En = 0.0, En1 = 0.0;
+        if (active) {
+            En = E[row + n - sample_base];
+            En1 = E[row + n + 1 - sample_base];
+        }
+        const double Eb = 0.5 * (En + En1);
+
+        // forward elimination (scaled variables as in the 32-wide path)
+        {
+            auto load_row = [&](int rr) -> Cx {
+                const int j = base + rr;
+                return (rr < nrows && (unsigned)j < (unsigned)N) ? ld_cg(ps + (int64_t)j * I + i) : mk(R(0), R(0));
+            };
+            double cr = 0.0, ci = 0.0;
+            R Dr = 0, Di = 0;
+            Cx pa = load_row(0), pb = load_row(1);
+            Cx* r = sc;
+            for (int rr = 0; rr < nrows; ++rr) {
+                const Cx p = pa;
+                pa = pb;
+                pb = load_row(rr + 2);
+                const int j = base + rr;
+                const bool in = (unsigned)j < (unsigned)N;
+                const double2 t = __ldg(tab_ab2 + min(max(j, 0), N - 1));
+                const double Qr = inv_beta + ci;
+                const double Qi = fma(t.y, Eb, t.x) - cr;
+                const double inv = kMixed ? rcp_pos_2nd(fma(Qr, Qr, Qi * Qi)) : rcp_pos(fma(Qr, Qr, Qi * Qi));
+                cr = in ? Qi * inv : 0.0;
+                ci = in ? Qr * inv : 0.0;
+                R gr, gi;
+                if constexpr (kMixed) {
+                    gr = d2f(cr);
+                    gi = d2f(ci);
+                } else {
+                    gr = cr;
+                    gi = ci;
+                }
+                const R ur = p.x - Di;
+                const R ui = p.y + Dr;
+                Dr = in ? fma(gr, ui, gi * ur) : R(0);
+                Di = in ? fma(gi, ui, -gr * ur) : R(0);
+                r[lane] = mk(gr, gi);
+                r[kLanes + lane] = mk(Dr, Di);
+                r += 2 * kLanes;
+            }
+        }
+        __syncthreads();   // every read of psi^n precedes any write of psi^{n+1}
+
+        // back substitution over rows nrows-1 .. K; own segment rows K .. K+m-1
+        ObsSums o{0.0, 0.0, 0.0};
+        {
+            R Yr = 0, Yi = 0;
+            const Cx* r = sc + (int64_t)(nrows - 1) * (2 * kLanes);
+#pragma unroll 2
+            for (int rr = nrows - 1; rr >= K; --rr) {
+                const int j = base + rr;
+                const Cx g2 = r[lane];
+                const Cx d2 = r[kLanes + lane];
+                r -= 2 * kLanes;
+                const R nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
+                const R ni = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
+                Yr = j < N ? nr : R(0);   // Dirichlet restart at the far wall
+                Yi = j < N ? ni : R(0);
+                if (rr < K + m && j < N) {
+                    Cx* pw = ps + (int64_t)j * I + i;
+                    const Cx old = ld_cg(pw);
+                    R xr = fma(two_over_beta, Yr, -old.x);
+                    R xi = fma(two_over_beta, Yi, -old.y);
+                    if (j < jm_lo || j > jm_hi) {
+                        const R mm = (R)__ldg(tab_m + j);
+                        xr *= mm;
+                        xi *= mm;
+                    }
+                    if (active) *pw = mk(xr, xi);
+                    const double rho = fma((double)xr, (double)xr, (double)xi * (double)xi);
+                    const double2 xv = __ldg(tab_xv2 + j);
+                    o.n += rho;
+                    o.x = fma(xv.x, rho, o.x);
+                    o.v = fma(xv.y, rho, o.v);
+                }
+            }
+        }
+        const ObsSums t = reduce_obs(lane_sum(o), red, P);   // its barrier orders this step's writes
+        if (w == 0 && q == 0 && active) {
+            const int64_t kk = row + n + 1 - sample_base;
+            d_out[kk] = t.x * dx;
+            a_out[kk] = fma(En1, t.n, t.v) * dx;
+            if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
+        }
+    }
+}
+
 template <bool kMixed>
 __global__ void __launch_bounds__(512, 1)
 k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const ClassDesc* __restrict__ cls,
@@ -78,7 +232,7 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const GroupDesc G = groups[g];
         const ClassDesc C = cls[G.cls];
         const int N = G.N, Pg = G.P, K = G.K, m = G.m;
-        const int64_t slot = G.slot0 + lane;
+        const int64_t slot = G.slot0 + (lane & (G.I - 1));   // this lane's instance
         const int64_t nt = slot_nt[slot];   // -1 for padding lanes
         const int64_t row = slot_row[slot];
         const double beta = C.beta;
@@ -101,6 +255,11 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const int64_t n0 = step_begin + (int64_t)kslice * slice;
         const int64_t n1 = min(n_end, n0 + slice);
 
+        if (G.I != kLanes) {
+            split_slice<kMixed>(G, ps, tab_ab2, tab_xv2, tab_m, inv_beta, two_over_beta, dx, jm_lo, jm_hi,
+                                nt, row, slot, n0, n1, kslice == 0 && step_begin == 0, E, d_out, a_out,
+                                sample_base, sc, red, status);
+        } else {
         if (kslice == 0 && step_begin == 0) {
             // observables of the initial state
             ObsSums o{0.0, 0.0, 0.0};
@@ -340,8 +499,9 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
             }
         }
+        }   // 32-wide group
 
-        if (timed_out) status[G.slot0 + lane] = 2;   // a bulk copy did not complete in time
+        if (timed_out) status[slot] = 2;   // a bulk copy did not complete in time
 
         // release the group: its psi writes become visible before the next owner's claim
         __threadfence();

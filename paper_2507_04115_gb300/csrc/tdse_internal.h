@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "tdse.h"
+
 namespace tdse {
 
 constexpr int kLanes = 32;          // instances per group: one per lane of a warp
@@ -28,15 +30,18 @@ struct ClassDesc {
     double rho;           // NUMEROV_SPLIT: max_j max(|L_j|, |C_j|), the decay rate of its sweeps
 };
 
-// A group = 32 instances of one class, one per lane.  The propagation kernel processes a group
-// with one CTA at a time (P warps, the group uses the first P_g of them).
+// A group = I instances of one class.  With I = 32 every lane of a warp carries its own instance;
+// with I = 32/L each instance spans L lanes of every warp, lane l holding instance l % I and the
+// segment l / I of the warp's L (lane split, for batches too small to fill the GPU with 32-wide
+// groups).  The propagation kernel processes a group with one CTA at a time (P warps, the group
+// uses the first P_g of them), so an instance is cut into P_g * L segments of m points.
 struct GroupDesc {
-    int64_t psi_off;      // complex-element offset of the group's wavefunctions, layout [N][32]
-    int64_t slot0;        // first slot (slot = group * 32 + lane)
+    int64_t psi_off;      // complex-element offset of the group's wavefunctions, layout [N][I]
+    int64_t slot0;        // first slot (slot = slot0 + instance index within the group)
     int64_t nt_max;       // largest Nt over the group's real instances
     int32_t cls;          // class index
-    int32_t N, P, K, m;   // grid size, segments used (<= warps per CTA), halo, segment length
-    int32_t pad;
+    int32_t N, P, K, m;   // grid size, warps carrying segments, halo, segment length
+    int32_t I;            // instances per group (32, 16, 8, 4, 2 or 1)
 };
 
 // Device-side tables offsets inside a class block (in doubles).
@@ -73,8 +78,14 @@ inline int class_segments(int N, int K, int warps)
     return std::max(1, std::min(warps, max_P));
 }
 
+// Segment length of a group: P_g warps x L lanes per instance share the N points.
+inline int group_segment_length(int N, int P, int L) { return (N + P * L - 1) / (P * L); }
+
 // Stores the calling thread's last-error message (tdse_api.cu).
 const char* set_error_message(const char* msg);
+
+// CUDA device a batch was created on (for host code layered on the public calls).
+int batch_device(const tdse_batch* b);
 
 // ---- kernel launchers (tdse_kernels.cu); all return cudaGetLastError() after the launch ----
 
@@ -121,9 +132,9 @@ cudaError_t launch_propagate_numerov(int mixed, const GroupDesc* d_groups, int64
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, double dt,
                                      int* d_busy, int* d_progress, int* d_status, cudaStream_t st);
 
-cudaError_t launch_get_psi(int mixed, const void* d_psi, int64_t psi_off, int N, int lane, double* out,
+cudaError_t launch_get_psi(int mixed, const void* d_psi, int64_t psi_off, int N, int lane, int I, double* out,
                            cudaStream_t st);
-cudaError_t launch_set_psi(int mixed, void* d_psi, int64_t psi_off, int N, int lane, const double* in, cudaStream_t st);
+cudaError_t launch_set_psi(int mixed, void* d_psi, int64_t psi_off, int N, int lane, int I, const double* in, cudaStream_t st);
 
 cudaError_t launch_spectrum(const double* a, const int64_t* d_offsets, int64_t n_rows, double dt, int64_t k_begin,
                             int64_t k_end, double* S, cudaStream_t st);

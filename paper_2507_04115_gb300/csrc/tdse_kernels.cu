@@ -215,11 +215,16 @@ __global__ void k_broadcast_psi(const GroupDesc* groups, int64_t n_groups, const
     const int lane = threadIdx.x & 31;
     for (int64_t g = blockIdx.y; g < n_groups; g += gridDim.y) {
         const GroupDesc G = groups[g];
-        if (!slot_valid[G.slot0 + lane]) continue;
+        // a warp covers 32 / I consecutive points of the [N][I] layout
+        const int i = lane % G.I, jq = lane / G.I, per_warp = kLanes / G.I;
+        if (!slot_valid[G.slot0 + i]) continue;
         const double* src = work + work_off[G.cls];
         Cx* dst = psi + G.psi_off;
-        for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < G.N; j += gridDim.x * (blockDim.x >> 5))
-            store_cx(dst + (int64_t)j * kLanes + lane, src[j], 0.0);
+        for (int j0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per_warp; j0 < G.N;
+             j0 += gridDim.x * (blockDim.x >> 5) * per_warp) {
+            const int j = j0 + jq;
+            if (j < G.N) store_cx(dst + (int64_t)j * G.I + i, src[j], 0.0);
+        }
     }
 }
 
@@ -241,38 +246,38 @@ cudaError_t launch_broadcast_psi(int mixed, const GroupDesc* d_groups, int64_t n
 // ------------------------------------------------------------------------------------ psi access
 
 template <class Cx>
-__global__ void k_get_psi(const Cx* psi, int64_t off, int N, int lane, double* out)
+__global__ void k_get_psi(const Cx* psi, int64_t off, int N, int lane, int I, double* out)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-        const Cx v = psi[off + (int64_t)j * kLanes + lane];
+        const Cx v = psi[off + (int64_t)j * I + lane];
         out[2 * j] = v.x;
         out[2 * j + 1] = v.y;
     }
 }
 
 template <class Cx>
-__global__ void k_set_psi(Cx* psi, int64_t off, int N, int lane, const double* in)
+__global__ void k_set_psi(Cx* psi, int64_t off, int N, int lane, int I, const double* in)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x)
-        store_cx(psi + off + (int64_t)j * kLanes + lane, in[2 * j], in[2 * j + 1]);
+        store_cx(psi + off + (int64_t)j * I + lane, in[2 * j], in[2 * j + 1]);
 }
 
-cudaError_t launch_get_psi(int mixed, const void* d_psi, int64_t psi_off, int N, int lane, double* out,
+cudaError_t launch_get_psi(int mixed, const void* d_psi, int64_t psi_off, int N, int lane, int I, double* out,
                            cudaStream_t st)
 {
     if (mixed)
-        k_get_psi<float2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<const float2*>(d_psi), psi_off, N, lane, out);
+        k_get_psi<float2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<const float2*>(d_psi), psi_off, N, lane, I, out);
     else
-        k_get_psi<double2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<const double2*>(d_psi), psi_off, N, lane, out);
+        k_get_psi<double2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<const double2*>(d_psi), psi_off, N, lane, I, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_psi(int mixed, void* d_psi, int64_t psi_off, int N, int lane, const double* in, cudaStream_t st)
+cudaError_t launch_set_psi(int mixed, void* d_psi, int64_t psi_off, int N, int lane, int I, const double* in, cudaStream_t st)
 {
     if (mixed)
-        k_set_psi<float2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<float2*>(d_psi), psi_off, N, lane, in);
+        k_set_psi<float2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<float2*>(d_psi), psi_off, N, lane, I, in);
     else
-        k_set_psi<double2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<double2*>(d_psi), psi_off, N, lane, in);
+        k_set_psi<double2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<double2*>(d_psi), psi_off, N, lane, I, in);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,52 @@ __global__ void k_cvt(double* out, int iters, double a)
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// A reciprocal seed without the double approximation: 1/n from the float approximation
+// (rcp.approx.ftz.f32, XU pipe) of n truncated to 20 mantissa bits, narrowed and widened by
+// integer arithmetic on the exponent field (double bias 1023 -> float bias 127: a shift of 896);
+// relative error < 2^-20 + 2^-23 inside float's normal range.  Probed as an alternative to
+// rcp.approx.ftz.f64 (the two measure the same cost, so the kernels keep the hardware seed).
+__device__ __forceinline__ double rcp_seed_f32(double n)
+{
+    const int hi = __double2hiint(n);
+    const float f = __int_as_float((hi - (896 << 20)) << 3);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(f));
+    const int yb = __float_as_int(yf);
+    return __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
+}
+
+// 8 independent FMA chains; with kSeed > 0 every FMA result also feeds a reciprocal seed
+// (1: rcp.approx.ftz.f64, 2: rcp_seed_f32) summed into a second accumulator
+// by an FMA, so that the loop's extra time over kSeed = 0 is one seed plus one FMA per element.
+template <int kSeed>
+__global__ void k_seed(double* out, int iters, double a, double b)
+{
+    double acc[8], sum[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        acc[c] = 1.0 + threadIdx.x * 1e-3 + c;
+        sum[c] = 0.0;
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            acc[c] = fma(acc[c], a, b);
+            if constexpr (kSeed == 1) {
+                double y;
+                asm volatile("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(acc[c]));
+                sum[c] = fma(y, a, sum[c]);
+            } else if constexpr (kSeed == 2) {
+                sum[c] = fma(rcp_seed_f32(acc[c]), a, sum[c]);
+            }
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += acc[c] + sum[c];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" tdse_status tdse_probe_pipes(int device, tdse_pipe_rates* out)
@@ -109,6 +155,16 @@ extern "C" tdse_status tdse_probe_pipes(int device, tdse_pipe_rates* out)
         ms = timed([&] { k_cvt<<<blocks, threads>>>(buf, itc, 1e-9); });
         // per element: one double->float, one float->double, one double add
         out->cvt_pairs_per_s = 8.0 * itc * (double)blocks * threads / (ms * 1e-3);
+        {
+            // acc stays near b / (1 - a) = 1 (a = 0.999, b = 1e-3): inside every seed's range
+            const int its = 1024;
+            const double t0 = timed([&] { k_seed<0><<<blocks, threads>>>(buf, its, 0.999, 1e-3); });
+            const double t1 = timed([&] { k_seed<1><<<blocks, threads>>>(buf, its, 0.999, 1e-3); });
+            const double t2 = timed([&] { k_seed<2><<<blocks, threads>>>(buf, its, 0.999, 1e-3); });
+            // t0 = one FMA per element; the extra FMA of the seeded loops is subtracted
+            out->rcp_f64_approx_fma_slots = (t1 - t0) / t0 - 1.0;
+            out->rcp_seed_fma_slots = (t2 - t0) / t0 - 1.0;
+        }
         out->sm_count = sms;
         out->sm_clock_mhz = clk_khz / 1000.0;
         if (cudaGetLastError() != cudaSuccess) {

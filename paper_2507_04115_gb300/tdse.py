@@ -21,7 +21,7 @@ _lib = None
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
-           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_last_error")
+           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -36,14 +36,21 @@ class tdse_absorber(ctypes.Structure):
 class tdse_plan_info(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int64), ("segments", ctypes.c_int32), ("halo", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas", ctypes.c_int32), ("slice_steps", ctypes.c_int32),
-                ("scratch_bytes", ctypes.c_int64), ("psi_bytes", ctypes.c_int64)]
+                ("scratch_bytes", ctypes.c_int64), ("psi_bytes", ctypes.c_int64),
+                ("lanes_per_instance", ctypes.c_int32)]
 
 
 class tdse_pipe_rates(ctypes.Structure):
     _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp64_warp_instr_per_s", ctypes.c_double),
                 ("fp64_one_lane_warp_instr_per_s", ctypes.c_double),
                 ("fp64_tflops_warps_per_sm", ctypes.c_double * 3), ("fp32_fma_tflops", ctypes.c_double),
-                ("cvt_pairs_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32), ("sm_clock_mhz", ctypes.c_double)]
+                ("cvt_pairs_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32), ("sm_clock_mhz", ctypes.c_double),
+                ("rcp_f64_approx_fma_slots", ctypes.c_double), ("rcp_seed_fma_slots", ctypes.c_double)]
+
+
+class tdse_tune_trial(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("slice_steps", ctypes.c_int32),
+                ("ctas", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class TDSEError(RuntimeError):
@@ -83,6 +90,9 @@ def load(path: str | None = None):
     L.tdse_probe_pipes.argtypes = [ctypes.c_int, ctypes.POINTER(tdse_pipe_rates)]
     L.tdse_copy_state.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
     L.tdse_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp]
+    L.tdse_autotune.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.POINTER(tdse_tune_trial), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp]
+    L.tdse_set_layout.argtypes = [_vp, ctypes.c_int32]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -142,7 +152,7 @@ class Batch:
     """A batch of independent TDSE instances living on one GPU (see include/tdse.h)."""
 
     def __init__(self, N, dx, softening, n_steps, dt, charge=1.0, row_offsets=None, absorber=(20.0, 0.125),
-                 precision=TDSE_FP64, scheme=TDSE_FULL_CN, device=0):
+                 precision=TDSE_FP64, scheme=TDSE_FULL_CN, device=0, lanes_per_instance=0):
         N = np.atleast_1d(np.asarray(N, dtype=np.int64))
         n = N.size
         dx = np.broadcast_to(np.asarray(dx, dtype=np.float64), (n,))
@@ -159,6 +169,8 @@ class Batch:
         self.n_inst = n
         self._h = tdse_batch_create(list(zip(N, dx, a, Z)), self.n_steps, self.row_offsets, dt, absorber, precision,
                                     scheme, device)
+        if lanes_per_instance:
+            self.set_layout(lanes_per_instance)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -229,7 +241,12 @@ class Batch:
         _check(load().tdse_plan(self._h, ctypes.byref(info)))
         return dict(n_groups=info.n_groups, segments=info.segments, halo=info.halo,
                     warps_per_cta=info.warps_per_cta, ctas=info.ctas, slice_steps=info.slice_steps,
-                    scratch_bytes=info.scratch_bytes, psi_bytes=info.psi_bytes)
+                    scratch_bytes=info.scratch_bytes, psi_bytes=info.psi_bytes,
+                    lanes_per_instance=info.lanes_per_instance)
+
+    def set_layout(self, lanes_per_instance=0):
+        """Lanes per instance of the layout (see tdse_set_layout; 0 = cost model).  Discards the state."""
+        _check(load().tdse_set_layout(self._h, int(lanes_per_instance)))
 
     def save_state(self, stream=None):
         """Device copy of every wavefunction (opaque layout; see tdse_copy_state)."""
@@ -250,6 +267,21 @@ class Batch:
         _check(load().tdse_adjoint(self._h, _dev_ptr(E, "E"), _dev_ptr(gd, "gd"), _dev_ptr(ga, "ga"),
                                    _dev_ptr(gE, "gE"), int(ckpt_every), _stream_ptr(stream)))
         return gE
+
+    def autotune(self, E, d, a, step_begin=0, step_end=None, sample_base=0, repeats=1, stream=None):
+        """Time candidate launch shapes on steps [step_begin, step_end) of the field rows E (d and a
+        rows there are overwritten) and keep the fastest (see tdse_autotune).  The batch's state is
+        unchanged.  Returns the trials as dicts, in the order run."""
+        if step_end is None:
+            step_end = int(self.n_steps.max())
+        cap = 64
+        trials = (tdse_tune_trial * cap)()
+        n = ctypes.c_int32(0)
+        _check(load().tdse_autotune(self._h, _dev_ptr(E, "E"), _dev_ptr(d, "d"), _dev_ptr(a, "a"), int(sample_base),
+                                    int(step_begin), int(step_end), int(repeats), trials, cap, ctypes.byref(n),
+                                    _stream_ptr(stream)))
+        return [dict(warps_per_cta=t.warps_per_cta, ctas_per_sm=t.ctas_per_sm, slice_steps=t.slice_steps,
+                     ctas=t.ctas, ms=float(t.ms)) for t in trials[: min(n.value, cap)]]
 
     def set_launch(self, warps_per_cta=0, ctas_per_sm=0, slice_steps=0, max_ctas=0):
         """Override the persistent grid (see tdse_set_launch); 0 keeps a default."""
@@ -287,7 +319,8 @@ def tdse_probe_pipes(device=0):
     return dict(fp64_fma_tflops=r.fp64_fma_tflops, fp64_warp_instr_per_s=r.fp64_warp_instr_per_s,
                 fp64_one_lane_warp_instr_per_s=r.fp64_one_lane_warp_instr_per_s,
                 fp64_tflops_warps_per_sm=list(r.fp64_tflops_warps_per_sm), fp32_fma_tflops=r.fp32_fma_tflops,
-                cvt_pairs_per_s=r.cvt_pairs_per_s, sm_count=r.sm_count, sm_clock_mhz=r.sm_clock_mhz)
+                cvt_pairs_per_s=r.cvt_pairs_per_s, sm_count=r.sm_count, sm_clock_mhz=r.sm_clock_mhz,
+                rcp_f64_approx_fma_slots=r.rcp_f64_approx_fma_slots, rcp_seed_fma_slots=r.rcp_seed_fma_slots)
 
 
 def _make_autograd():

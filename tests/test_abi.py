@@ -69,6 +69,9 @@ def test_null_handles_are_rejected(lib):
     offs = np.array([0, 4], dtype=np.int64)
     assert lib.tdse_spectrum(None, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1, 0.1, 0, 2, None,
                              None) == tdse.TDSE_ERR_ARG
+    n = ctypes.c_int32(-1)
+    assert lib.tdse_autotune(None, None, None, None, 0, 0, 4, 1, None, 0, ctypes.byref(n), None) == tdse.TDSE_ERR_ARG
+    assert n.value == -1
     lib.tdse_batch_destroy(None)
 
 

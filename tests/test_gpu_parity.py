@@ -34,9 +34,12 @@ def env():
     return tdse, oracle
 
 
-def _rel(x, ref, floor=1e-6):
-    """max |x - ref| / max(max |ref|, floor): the floor keeps rounding-level signals (a field-free
-    instance has <x> ~ 1e-16) from turning absolute agreement into a large relative number."""
+def _rel(x, ref, floor=1e-5):
+    """max |x - ref| / max(max |ref|, floor): the floor keeps rounding-level signals from turning
+    absolute agreement into a large relative number.  A symmetric state (the ground state, so an
+    instance with Nt = 0 or no field) has <x> = <dV/dx> = 0 exactly, and the computed values are
+    the rounding of a sum of N terms up to ~0.1 in magnitude, ~1e-15; a different summation order
+    (segments, lanes, warps) changes that noise, so such a series is compared at 1e-14 absolute."""
     return float(np.max(np.abs(np.asarray(x) - np.asarray(ref))) / max(np.max(np.abs(ref)), floor))
 
 
@@ -93,9 +96,11 @@ def test_single_atom_full_propagation(env):
     b.close()
 
 
-def test_ragged_batch_chunks_classes_and_segments(env):
-    """Ragged batch: 45 instances (not a multiple of 32), three grid classes, uneven Nt (including 0),
-    chunked calls with a moving sample_base, and every segment count the planner allows."""
+@pytest.mark.parametrize("lanes", [1, 2, 8, 32])
+def test_ragged_batch_chunks_classes_and_segments(env, lanes):
+    """Ragged batch: 45 instances (not a multiple of the group width), three grid classes, uneven Nt
+    (including 0), chunked calls with a moving sample_base, every segment count the planner allows
+    (32-wide groups) and the lane-split layouts (2, 8 and 32 lanes per instance)."""
     tdse, oracle = env
     from paper_2507_04115_gb300 import inputs
     rng = np.random.default_rng(11)
@@ -117,11 +122,15 @@ def test_ragged_batch_chunks_classes_and_segments(env):
         psi0, _, _ = oracle.ground_state(int(N[i]), dx[i], soft[i], **GS_KW)
         m = oracle.mask(int(N[i]), dx[i], 20.0, 0.125)
         refs.append(oracle.propagate(psi0, rows[i], dx[i], dt, soft[i], mask_values=m)[1:])
-    b = tdse.Batch(N, dx, soft, nt, dt, row_offsets=offs, absorber=(20.0, 0.125))
+    b = tdse.Batch(N, dx, soft, nt, dt, row_offsets=offs, absorber=(20.0, 0.125), lanes_per_instance=lanes)
+    assert b.plan()["lanes_per_instance"] == lanes
     # (warps per CTA, CTAs per SM, slice steps, CTA cap): exact single-segment Thomas, halo
     # segments, slices that do not divide the chunks, and fewer CTAs than groups so that groups
     # move between CTAs (and SMs) from one slice to the next
-    for launch in [(1, 1, 7, 2), (2, 2, 32, 0), (3, 1, 5, 1), (8, 1, 13, 2), (0, 0, 0, 0)]:
+    launches = [(1, 1, 7, 2), (2, 2, 32, 0), (3, 1, 5, 1), (8, 1, 13, 2), (0, 0, 0, 0)]
+    if lanes > 1:
+        launches = [(1, 1, 7, 2), (4, 1, 9, 3), (0, 0, 0, 0)]
+    for launch in launches:
         b.set_launch(*launch)
         b.ground_state(**GS_KW)
         d = torch.full_like(Et, np.nan)
@@ -329,8 +338,10 @@ def test_mixed_single_atom_against_fp64_oracle(env):
     b.close()
 
 
-def test_mixed_ragged_batch_segments(env):
-    """MIXED on a ragged multi-class batch with halos, migration between CTAs and chunked calls."""
+@pytest.mark.parametrize("lanes", [1, 8])
+def test_mixed_ragged_batch_segments(env, lanes):
+    """MIXED on a ragged multi-class batch with halos, migration between CTAs and chunked calls
+    (32-wide groups with the bulk-copy ring, and lane-split groups)."""
     tdse, oracle = env
     from paper_2507_04115_gb300 import inputs
     rng = np.random.default_rng(12)
@@ -346,8 +357,9 @@ def test_mixed_ragged_batch_segments(env):
     offs = np.concatenate([[0], np.cumsum(nt + 1)])
     dev = torch.device("cuda", 0)
     Et = _device_rows(rows, offs, dev)
-    b = tdse.Batch(N, dx, soft, nt, dt, row_offsets=offs, absorber=(20.0, 0.125), precision=tdse.TDSE_MIXED)
-    b.set_launch(4, 1, 9, 1)
+    b = tdse.Batch(N, dx, soft, nt, dt, row_offsets=offs, absorber=(20.0, 0.125), precision=tdse.TDSE_MIXED,
+                   lanes_per_instance=lanes)
+    b.set_launch(4, 1, 9, 1 if lanes == 1 else 3)
     b.ground_state(**GS_KW)
     d = torch.full_like(Et, np.nan)
     acc = torch.full_like(Et, np.nan)
@@ -419,10 +431,12 @@ def test_numerov_split_mixed_matches_oracle(env):
 
 # ------------------------------------------------------------------------------- adjoint
 
-def test_adjoint_matches_oracle_and_finite_differences(env):
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_adjoint_matches_oracle_and_finite_differences(env, lanes):
     """dL/dE from the adjoint kernel against the oracle's exact discrete adjoint, on a ragged batch
-    with checkpoint intervals that do not divide the lengths and groups sharing CTAs; then a
-    harmonic-window loss through torch autograd against central differences of the forward kernel."""
+    with checkpoint intervals that do not divide the lengths and groups sharing CTAs (32-wide and
+    lane-split groups); then a harmonic-window loss through torch autograd against central
+    differences of the forward kernel."""
     tdse, oracle = env
     from paper_2507_04115_gb300 import inputs
     rng = np.random.default_rng(31)
@@ -436,8 +450,8 @@ def test_adjoint_matches_oracle_and_finite_differences(env):
     Et = _device_rows(rows, offs, dev)
     gd = torch.from_numpy(rng.standard_normal(int(offs[-1]))).to(dev)
     ga = torch.from_numpy(rng.standard_normal(int(offs[-1]))).to(dev)
-    b = tdse.Batch([N] * n, dx, a, nt, dt, row_offsets=offs, absorber=(20.0, 0.125))
-    b.set_launch(3, 1, 0, 1)
+    b = tdse.Batch([N] * n, dx, a, nt, dt, row_offsets=offs, absorber=(20.0, 0.125), lanes_per_instance=lanes)
+    b.set_launch(3, 1, 0, 1 if lanes == 1 else 2)
     b.ground_state(**GS_KW)
     psi0, _, _ = oracle.ground_state(N, dx, a, **GS_KW)
     m = oracle.mask(N, dx, 20.0, 0.125)
@@ -558,3 +572,68 @@ def test_chunked_propagation_replays_from_a_cuda_graph(env):
         torch.cuda.synchronize()
         assert torch.equal(d_g, d_ref) and torch.equal(a_g, a_ref)
     b.close()
+
+
+# ------------------------------------------------------------------------------- lane-split layout
+
+def test_layout_cost_model_and_psi_access(env):
+    """The cost model keeps 32 instances per warp for a batch that fills the GPU and splits
+    instances over lanes for small batches; get/set_psi address the [N][I] layouts."""
+    tdse, oracle = env
+    big = tdse.Batch([4096] * 8192, 0.15, 1.19, [10] * 8192, 0.02)
+    assert big.plan()["lanes_per_instance"] == 1
+    big.close()
+    mid = tdse.Batch([2048] * 1024, 0.15, 1.19, [10] * 1024, 0.02)
+    assert mid.plan()["lanes_per_instance"] == 4
+    mid.close()
+    one = tdse.Batch([2000], 0.2, 1.19, [10], 0.05)
+    assert one.plan()["lanes_per_instance"] == 32
+    one.close()
+    # Numerov keeps 32-wide groups whatever is requested
+    nb = tdse.Batch([512] * 3, 0.2, 1.19, [10] * 3, 0.05, scheme=tdse.TDSE_NUMEROV_SPLIT, lanes_per_instance=8)
+    assert nb.plan()["lanes_per_instance"] == 1
+    nb.close()
+    rng = np.random.default_rng(3)
+    for lanes in (1, 8, 32):
+        b = tdse.Batch([300, 300, 520], 0.2, 1.2, [5, 5, 5], 0.05, lanes_per_instance=lanes)
+        vals = []
+        for i, N in enumerate((300, 300, 520)):
+            v = torch.from_numpy(rng.standard_normal(N) + 1j * rng.standard_normal(N)).to("cuda")
+            b.set_psi(i, v)
+            vals.append(v)
+        for i in range(3):
+            assert torch.equal(b.get_psi(i), vals[i])
+        b.close()
+    b = tdse.Batch([300], 0.2, 1.2, [5], 0.05)
+    with pytest.raises(tdse.TDSEError):
+        b.set_layout(3)
+    b.close()
+
+
+def test_lane_split_matches_32_wide(env):
+    """The same batch under every layout gives the same series to rounding of the halo truncation
+    (both are within 1e-18 of the exact Thomas solve, far below the parity tolerance)."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    rng = np.random.default_rng(5)
+    n = 9
+    N, dx, dt, a = 1200, 0.15, 0.02, 1.19
+    nt = rng.integers(300, 500, n)
+    rows = [inputs.sin2_pulse(int(k), dt, rng.uniform(0.04, 0.09), 0.057, 1.0, rng.uniform(0, 6)) for k in nt]
+    offs = np.concatenate([[0], np.cumsum(nt + 1)])
+    Et = _device_rows(rows, offs, torch.device("cuda", 0))
+    outs = {}
+    for lanes in (1, 2, 4, 16, 32):
+        b = tdse.Batch([N] * n, dx, a, nt, dt, row_offsets=offs, absorber=(20.0, 0.125), lanes_per_instance=lanes)
+        b.ground_state(**GS_KW)
+        d, acc = torch.zeros_like(Et), torch.zeros_like(Et)
+        b.propagate(Et, d, acc)
+        torch.cuda.synchronize()
+        assert b.check() == -1
+        outs[lanes] = (d.cpu().numpy(), acc.cpu().numpy())
+        b.close()
+    for lanes in (2, 4, 16, 32):
+        for i in range(n):
+            sl = slice(offs[i], offs[i + 1])
+            assert _rel(outs[lanes][0][sl], outs[1][0][sl]) < 1e-11, (lanes, i)
+            assert _rel(outs[lanes][1][sl], outs[1][1][sl]) < 1e-11, (lanes, i)
