@@ -282,6 +282,11 @@ typedef struct {
     double sm_clock_mhz;
     double rcp_f64_approx_fma_slots;
     double rcp_seed_fma_slots;
+    double dadd_fma_slots;   /* time of an FP64 add, a multiply, in units of an FP64 FMA */
+    double dmul_fma_slots;
+    double add_as_fma_slots; /* the add as fma(x, 1, y), the multiply as fma(x, y, -0), with 1 and -0 not known at compile time */
+    double mul_as_fma_slots;
+    double fma_repeat_slots; /* the FMA loop timed again last (clock drift check) */
 } tdse_pipe_rates;
 
 tdse_status tdse_probe_pipes(int device, tdse_pipe_rates* out_host);

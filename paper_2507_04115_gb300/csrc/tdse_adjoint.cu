@@ -30,11 +30,13 @@ namespace {
 struct AdjGeom {
     int N, I, i, q, base, nrows, K, m, s, e;
     double inv_beta, two_over_beta;
+    Fma64 F;
     __device__ __forceinline__ int64_t at(int j) const { return (int64_t)j * I + i; }
 };
 
-__device__ __forceinline__ AdjGeom adj_geom(const GroupDesc& G, double beta)
+__device__ __forceinline__ AdjGeom adj_geom(const GroupDesc& G, const ClassDesc& C)
 {
+    const double beta = C.beta;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     AdjGeom g;
     g.N = G.N;
@@ -51,6 +53,7 @@ __device__ __forceinline__ AdjGeom adj_geom(const GroupDesc& G, double beta)
     g.e = w < G.P ? min(G.N, sigma * G.m + G.m) : G.N;
     g.inv_beta = 1.0 / beta;
     g.two_over_beta = 2.0 / beta;
+    g.F = Fma64{C.one, C.nzero};
     return g;
 }
 
@@ -80,15 +83,16 @@ __device__ __forceinline__ void eliminate(const AdjGeom& g, double Eb, const dou
         const int jc = min(max(j, 0), g.N - 1);
         const double2 v = in ? rhs(jc) : make_double2(0.0, 0.0);
         const double2 t = __ldg(tab_ab2 + jc);
-        const double Qr = g.inv_beta + ci;
-        const double Qi = fma(t.y, Eb, t.x) - cr;
-        const double inv = rcp_pos(fma(Qr, Qr, Qi * Qi));
-        cr = in ? Qi * inv : 0.0;
-        ci = in ? Qr * inv : 0.0;
-        const double ur = v.x - Di;
-        const double ui = v.y + Dr;
-        Dr = in ? fma(cr, ui, ci * ur) : 0.0;
-        Di = in ? fma(ci, ui, -cr * ur) : 0.0;
+        const Fma64& F = g.F;
+        const double Qr = F.add(ci, g.inv_beta);
+        const double Qi = F.sub(fma(t.y, Eb, t.x), cr);
+        const double inv = rcp_pos(fma(Qr, Qr, F.mul(Qi, Qi)));
+        cr = in ? F.mul(Qi, inv) : 0.0;
+        ci = in ? F.mul(Qr, inv) : 0.0;
+        const double ur = F.sub(v.x, Di);
+        const double ui = F.add(v.y, Dr);
+        Dr = in ? fma(cr, ui, F.mul(ci, ur)) : 0.0;
+        Di = in ? fma(ci, ui, F.mul(-cr, ur)) : 0.0;
         r[lane] = make_double2(cr, ci);
         r[kLanes + lane] = make_double2(Dr, Di);
         r += 2 * kLanes;
@@ -132,8 +136,8 @@ __device__ __forceinline__ void fwd_step(double2* __restrict__ ps, const AdjGeom
         if (tape) tape[g.at(j)] = active ? make_double2(xr, xi) : old;
         if (j < jm_lo || j > jm_hi) {
             const double mm = __ldg(tab_m + j);
-            xr *= mm;
-            xi *= mm;
+            xr = g.F.mul(xr, mm);
+            xi = g.F.mul(xi, mm);
         }
         if (active) *pp = make_double2(xr, xi);
     });
@@ -181,7 +185,7 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
 
         const GroupDesc G = groups[gi];
         const ClassDesc C = cls[G.cls];
-        const AdjGeom geo = adj_geom(G, C.beta);
+        const AdjGeom geo = adj_geom(G, C);
         const int N = G.N, L = kLanes / G.I;
         const int64_t slot = G.slot0 + geo.i;
         const int64_t nt = slot_nt[slot];

@@ -472,6 +472,8 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
             C.a = I.softening;
             C.Z = I.charge;
             C.beta = dt / (4.0 * I.dx * I.dx);
+            C.one = 1.0;
+            C.nzero = -0.0;
             b->classes.push_back(C);
         } else {
             c = it->second;

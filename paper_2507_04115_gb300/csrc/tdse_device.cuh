@@ -29,6 +29,22 @@ __device__ __forceinline__ double rcp_pos_2nd(double n)
     return fma(y, e, y);
 }
 
+// FP64 add, subtract and multiply issued as fused multiply-adds.  On this GPU a DADD or DMUL
+// warp instruction occupies the FP64 pipe about 19 % longer than a DFMA (tdse_probe_pipes:
+// dadd_fma_slots, dmul_fma_slots), while fma(x, 1, y) = x + y, fma(y, -1, x) = x - y and
+// fma(x, y, -0) = x y hold exactly (one rounding of the exact result, signed zeros included).
+// The 1 and -0 are read from memory (the class descriptor) so that the compiler cannot fold the
+// FMAs back into adds and multiplies.  Float overloads keep the native FP32 operations.
+struct Fma64 {
+    double one, nzero;
+    __device__ __forceinline__ double add(double x, double y) const { return fma(x, one, y); }
+    __device__ __forceinline__ double sub(double x, double y) const { return fma(y, -one, x); }
+    __device__ __forceinline__ double mul(double x, double y) const { return fma(x, y, nzero); }
+    __device__ __forceinline__ float add(float x, float y) const { return x + y; }
+    __device__ __forceinline__ float sub(float x, float y) const { return x - y; }
+    __device__ __forceinline__ float mul(float x, float y) const { return x * y; }
+};
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll

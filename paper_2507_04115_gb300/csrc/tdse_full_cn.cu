@@ -37,7 +37,7 @@ namespace tdse {
 // warps.  No bulk copies on this path (it serves small batches, where the FP64 elimination is the
 // bound in both precisions); MIXED sums the observables in double directly.
 template <bool kMixed>
-__device__ __forceinline__ void split_slice(const GroupDesc& G, typename Prec<kMixed>::C* __restrict__ ps,
+__device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, typename Prec<kMixed>::C* __restrict__ ps,
                                             const double2* __restrict__ tab_ab2, const double2* __restrict__ tab_xv2,
                                             const double* __restrict__ tab_m, double inv_beta,
                                             typename Prec<kMixed>::R two_over_beta, double dx, int jm_lo, int jm_hi,
@@ -113,11 +113,12 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, typename Prec<kM
                 const int j = base + rr;
                 const bool in = (unsigned)j < (unsigned)N;
                 const double2 t = __ldg(tab_ab2 + min(max(j, 0), N - 1));
-                const double Qr = inv_beta + ci;
-                const double Qi = fma(t.y, Eb, t.x) - cr;
-                const double inv = kMixed ? rcp_pos_2nd(fma(Qr, Qr, Qi * Qi)) : rcp_pos(fma(Qr, Qr, Qi * Qi));
-                cr = in ? Qi * inv : 0.0;
-                ci = in ? Qr * inv : 0.0;
+                const double Qr = F.add(ci, inv_beta);
+                const double Qi = F.sub(fma(t.y, Eb, t.x), cr);
+                const double q2 = fma(Qr, Qr, F.mul(Qi, Qi));
+                const double inv = kMixed ? rcp_pos_2nd(q2) : rcp_pos(q2);
+                cr = in ? F.mul(Qi, inv) : 0.0;
+                ci = in ? F.mul(Qr, inv) : 0.0;
                 R gr, gi;
                 if constexpr (kMixed) {
                     gr = d2f(cr);
@@ -126,10 +127,10 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, typename Prec<kM
                     gr = cr;
                     gi = ci;
                 }
-                const R ur = p.x - Di;
-                const R ui = p.y + Dr;
-                Dr = in ? fma(gr, ui, gi * ur) : R(0);
-                Di = in ? fma(gi, ui, -gr * ur) : R(0);
+                const R ur = F.sub(p.x, Di);
+                const R ui = F.add(p.y, Dr);
+                Dr = in ? fma(gr, ui, F.mul(gi, ur)) : R(0);
+                Di = in ? fma(gi, ui, F.mul(-gr, ur)) : R(0);
                 r[lane] = mk(gr, gi);
                 r[kLanes + lane] = mk(Dr, Di);
                 r += 2 * kLanes;
@@ -159,13 +160,13 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, typename Prec<kM
                     R xi = fma(two_over_beta, Yi, -old.y);
                     if (j < jm_lo || j > jm_hi) {
                         const R mm = (R)__ldg(tab_m + j);
-                        xr *= mm;
-                        xi *= mm;
+                        xr = F.mul(xr, mm);
+                        xi = F.mul(xi, mm);
                     }
                     if (active) *pw = mk(xr, xi);
-                    const double rho = fma((double)xr, (double)xr, (double)xi * (double)xi);
+                    const double rho = fma((double)xr, (double)xr, F.mul((double)xi, (double)xi));
                     const double2 xv = __ldg(tab_xv2 + j);
-                    o.n += rho;
+                    o.n = F.add(rho, o.n);
                     o.x = fma(xv.x, rho, o.x);
                     o.v = fma(xv.y, rho, o.v);
                 }
@@ -231,6 +232,7 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
 
         const GroupDesc G = groups[g];
         const ClassDesc C = cls[G.cls];
+        const Fma64 F{C.one, C.nzero};
         const int N = G.N, Pg = G.P, K = G.K, m = G.m;
         const int64_t slot = G.slot0 + (lane & (G.I - 1));   // this lane's instance
         const int64_t nt = slot_nt[slot];   // -1 for padding lanes
@@ -256,7 +258,7 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const int64_t n1 = min(n_end, n0 + slice);
 
         if (G.I != kLanes) {
-            split_slice<kMixed>(G, ps, tab_ab2, tab_xv2, tab_m, inv_beta, two_over_beta, dx, jm_lo, jm_hi,
+            split_slice<kMixed>(G, F, ps, tab_ab2, tab_xv2, tab_m, inv_beta, two_over_beta, dx, jm_lo, jm_hi,
                                 nt, row, slot, n0, n1, kslice == 0 && step_begin == 0, E, d_out, a_out,
                                 sample_base, sc, red, status);
         } else {
@@ -312,13 +314,14 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     pnext += kLanes;
                     const double2 t = __ldg(tp);
                     ++tp;
-                    const double Qr = inv_beta + ci;
-                    const double Qi = fma(t.y, Eb, t.x) - cr;
+                    const double Qr = F.add(ci, inv_beta);
+                    const double Qi = F.sub(fma(t.y, Eb, t.x), cr);
                     // MIXED: gamma is rounded to float right after, so a 2^-40 reciprocal suffices
                     // (the recurrence damps an error by beta^2 per point; it stays ~1e-12)
-                    const double inv = kMixed ? rcp_pos_2nd(fma(Qr, Qr, Qi * Qi)) : rcp_pos(fma(Qr, Qr, Qi * Qi));
-                    cr = Qi * inv;
-                    ci = Qr * inv;
+                    const double q2 = fma(Qr, Qr, F.mul(Qi, Qi));
+                    const double inv = kMixed ? rcp_pos_2nd(q2) : rcp_pos(q2);
+                    cr = F.mul(Qi, inv);
+                    ci = F.mul(Qr, inv);
                     R gr, gi;
                     if constexpr (kMixed) {
                         gr = d2f(cr);
@@ -327,10 +330,10 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                         gr = cr;
                         gi = ci;
                     }
-                    const R ur = p.x - Di;
-                    const R ui = p.y + Dr;
-                    Dr = fma(gr, ui, gi * ur);
-                    Di = fma(gi, ui, -gr * ur);
+                    const R ur = F.sub(p.x, Di);
+                    const R ui = F.add(p.y, Dr);
+                    Dr = fma(gr, ui, F.mul(gi, ur));
+                    Di = fma(gi, ui, F.mul(-gr, ur));
                     r[lane] = mk(gr, gi);
                     r[kLanes + lane] = mk(Dr, Di);
                     r += 2 * kLanes;
@@ -475,16 +478,16 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     R xi = fma(two_over_beta, Yi, -old.y);
                     if (j < jm_lo || j > jm_hi) {
                         const R mm = __ldg(tm);
-                        xr *= mm;
-                        xi *= mm;
+                        xr = F.mul(xr, mm);
+                        xi = F.mul(xi, mm);
                     }
                     --tm;
                     if (active) *pw = mk(xr, xi);
                     pw -= kLanes;
-                    const R rho = fma(xr, xr, xi * xi);
+                    const R rho = fma(xr, xr, F.mul(xi, xi));
                     const double2 xv = __ldg(txv);
                     --txv;
-                    o.n += rho;
+                    o.n = F.add(rho, o.n);
                     o.x = fma(xv.x, rho, o.x);
                     o.v = fma(xv.y, rho, o.v);
                 }

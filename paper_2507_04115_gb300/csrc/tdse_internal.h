@@ -28,6 +28,7 @@ struct ClassDesc {
     double dx, a, Z;
     double beta;          // dt / (4 dx^2): magnitude of the off-diagonal of 1 + i dt/2 H
     double rho;           // NUMEROV_SPLIT: max_j max(|L_j|, |C_j|), the decay rate of its sweeps
+    double one, nzero;    // 1.0 and -0.0 as data, for adds and multiplies issued as FMAs (Fma64)
 };
 
 // A group = I instances of one class.  With I = 32 every lane of a warp carries its own instance;

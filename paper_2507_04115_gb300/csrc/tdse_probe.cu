@@ -59,6 +59,29 @@ __global__ void k_cvt(double* out, int iters, double a)
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// 8 independent chains of one FP64 operation (0: fma, 1: add, 2: mul) per element.
+template <int kOp>
+__global__ void k_op64(double* out, int iters, double a, double b, double one, double nzero)
+{
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 1.0 + threadIdx.x * 1e-3 + c;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if constexpr (kOp == 0) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(acc[c]) : "d"(a), "d"(b));
+            else if constexpr (kOp == 1) asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(acc[c]) : "d"(b));
+            else if constexpr (kOp == 2) asm volatile("mul.rn.f64 %0, %0, %1;" : "+d"(acc[c]) : "d"(a));
+            else if constexpr (kOp == 3) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(acc[c]) : "d"(one), "d"(b));
+            else asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(acc[c]) : "d"(a), "d"(nzero));
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += acc[c];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // A reciprocal seed without the double approximation: 1/n from the float approximation
 // (rcp.approx.ftz.f32, XU pipe) of n truncated to 20 mantissa bits, narrowed and widened by
 // integer arithmetic on the exponent field (double bias 1023 -> float bias 127: a shift of 896);
@@ -164,6 +187,20 @@ extern "C" tdse_status tdse_probe_pipes(int device, tdse_pipe_rates* out)
             // t0 = one FMA per element; the extra FMA of the seeded loops is subtracted
             out->rcp_f64_approx_fma_slots = (t1 - t0) / t0 - 1.0;
             out->rcp_seed_fma_slots = (t2 - t0) / t0 - 1.0;
+        }
+        {
+            const int its = 2048;
+            const double tf = timed([&] { k_op64<0><<<blocks, threads>>>(buf, its, 0.999, 1e-3, 1.0, -0.0); });
+            const double ta = timed([&] { k_op64<1><<<blocks, threads>>>(buf, its, 0.999, 1e-3, 1.0, -0.0); });
+            const double tm = timed([&] { k_op64<2><<<blocks, threads>>>(buf, its, 0.999, 1e-3, 1.0, -0.0); });
+            out->dadd_fma_slots = ta / tf;
+            out->dmul_fma_slots = tm / tf;
+            const double ta2 = timed([&] { k_op64<3><<<blocks, threads>>>(buf, its, 0.999, 1e-3, 1.0, -0.0); });
+            const double tm2 = timed([&] { k_op64<4><<<blocks, threads>>>(buf, its, 0.999, 1e-3, 1.0, -0.0); });
+            out->add_as_fma_slots = ta2 / tf;
+            out->mul_as_fma_slots = tm2 / tf;
+            const double tf2 = timed([&] { k_op64<0><<<blocks, threads>>>(buf, its, 0.999, 1e-3, 1.0, -0.0); });
+            out->fma_repeat_slots = tf2 / tf;
         }
         out->sm_count = sms;
         out->sm_clock_mhz = clk_khz / 1000.0;

@@ -113,6 +113,8 @@ extern "C" tdse_status tdse_propagate_static(const tdse_instance* inst_host, int
     C.a = I.softening;
     C.Z = I.charge;
     C.beta = dt / (4.0 * I.dx * I.dx);
+    C.one = 1.0;
+    C.nzero = -0.0;
     C.tab_off = 0;
     const int mask_on = absorber && absorber->width > 0.0;
     C.jm_lo = 0;

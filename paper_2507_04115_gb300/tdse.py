@@ -45,7 +45,10 @@ class tdse_pipe_rates(ctypes.Structure):
                 ("fp64_one_lane_warp_instr_per_s", ctypes.c_double),
                 ("fp64_tflops_warps_per_sm", ctypes.c_double * 3), ("fp32_fma_tflops", ctypes.c_double),
                 ("cvt_pairs_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32), ("sm_clock_mhz", ctypes.c_double),
-                ("rcp_f64_approx_fma_slots", ctypes.c_double), ("rcp_seed_fma_slots", ctypes.c_double)]
+                ("rcp_f64_approx_fma_slots", ctypes.c_double), ("rcp_seed_fma_slots", ctypes.c_double),
+                ("dadd_fma_slots", ctypes.c_double), ("dmul_fma_slots", ctypes.c_double),
+                ("add_as_fma_slots", ctypes.c_double), ("mul_as_fma_slots", ctypes.c_double),
+                ("fma_repeat_slots", ctypes.c_double)]
 
 
 class tdse_tune_trial(ctypes.Structure):
@@ -320,7 +323,10 @@ def tdse_probe_pipes(device=0):
                 fp64_one_lane_warp_instr_per_s=r.fp64_one_lane_warp_instr_per_s,
                 fp64_tflops_warps_per_sm=list(r.fp64_tflops_warps_per_sm), fp32_fma_tflops=r.fp32_fma_tflops,
                 cvt_pairs_per_s=r.cvt_pairs_per_s, sm_count=r.sm_count, sm_clock_mhz=r.sm_clock_mhz,
-                rcp_f64_approx_fma_slots=r.rcp_f64_approx_fma_slots, rcp_seed_fma_slots=r.rcp_seed_fma_slots)
+                rcp_f64_approx_fma_slots=r.rcp_f64_approx_fma_slots, rcp_seed_fma_slots=r.rcp_seed_fma_slots,
+                dadd_fma_slots=r.dadd_fma_slots, dmul_fma_slots=r.dmul_fma_slots,
+                add_as_fma_slots=r.add_as_fma_slots, mul_as_fma_slots=r.mul_as_fma_slots,
+                fma_repeat_slots=r.fma_repeat_slots)
 
 
 def _make_autograd():
