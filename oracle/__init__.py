@@ -16,6 +16,9 @@ Contents
 ``adjoint``: the exact discrete adjoint of the FULL_CN forward map (gradient of a loss of d and a
 with respect to every field sample).
 
+``energy_distribution``: the time-dependent electron energy distribution P(E) of a state through the
+resolvent of the field-free Hamiltonian (Sec. 6.1).
+
 Scheme ids: 0 = FULL_CN (E in the diagonal at the midpoint field), 1 = NUMEROV_SPLIT
 (the paper's Eqs. "CN - step 4/2/3").
 """
@@ -64,8 +67,10 @@ def lib():
                                        _dp, _dp, _dp]
         L.oracle_adjoint.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      _dp, _dp, ctypes.c_long, _dp, _dp, _dp, _dp]
+        L.oracle_energy_distribution.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
         for f in (L.oracle_grid, L.oracle_mask, L.oracle_energy, L.oracle_ground_state, L.oracle_propagate,
-                  L.oracle_adjoint):
+                  L.oracle_adjoint, L.oracle_energy_distribution):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -148,6 +153,17 @@ def adjoint(psi0, E, dx, dt, a, gd, ga, Z=1.0, mask_values=None):
                                 psi0.view(np.float64).ctypes.data_as(_dp), _ptr(gd), _ptr(ga), _ptr(gE)),
            "oracle_adjoint")
     return gE
+
+
+def energy_distribution(psi, E_grid, dx, a, eps, Z=1.0, scheme=FULL_CN):
+    """P(E_k) = N_eps eps^2 ||(E_k - H0 - i eps)^{-1} psi||^2, N_eps = 1/(pi eps), with the inversion in
+    the scheme's representation of H0 (Sec. 6.1; see oracle_energy_distribution)."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    Eg = np.ascontiguousarray(E_grid, dtype=np.float64)
+    P = np.zeros(Eg.size)
+    _check(lib().oracle_energy_distribution(psi.size, dx, a, Z, scheme, psi.view(np.float64).ctypes.data_as(_dp),
+                                            _ptr(Eg), Eg.size, eps, _ptr(P)), "oracle_energy_distribution")
+    return P
 
 
 def spectrum(acc, dt):

@@ -438,3 +438,62 @@ int oracle_adjoint(int N, double dx, double a, double Z, double dt, const double
     for (int k = 0; k < 3; ++k) { free(K[k]); free(M[k]); }
     return 0;
 }
+
+/* ---------------------------------------------------------------- energy distribution (Sec. 6.1) */
+
+/* Time-dependent electron energy distribution of a state psi (Sec. 6.1, the equations defining
+ * P(E, t) through the resolvent of the field-free Hamiltonian and its factorised form):
+ *     P(E) = N_eps eps^2 <psi| ((E - H0)^2 + eps^2)^{-1} |psi> = N_eps eps^2 || (E - H0 - i eps)^{-1} psi ||^2,
+ * with N_eps = 1 / (pi eps), the normalisation of a Lorentzian of half-width eps (so that the
+ * distribution of an eigenstate integrates to its norm), and || v ||^2 = sum_j |v_j|^2 dx.
+ * The inversion follows each scheme's representation of H0 = M^{-1} K (M, K from assemble):
+ *     (E - i eps - H0)^{-1} psi = ((E - i eps) M - K)^{-1} (M psi),
+ * i.e. the identity and the three-point H0 for FULL_CN, and the Numerov pencil for NUMEROV_SPLIT,
+ * solved with the Thomas algorithm.  Writes P[k] for the n_E energies E_grid[k]. */
+int oracle_energy_distribution(int N, double dx, double a, double Z, int scheme, const double* psi_ri,
+                               const double* E_grid, int n_E, double eps, double* P)
+{
+    if (N < 3 || !(dx > 0.0) || !(a > 0.0) || !(eps > 0.0) || n_E < 0 || !psi_ri || (n_E > 0 && (!E_grid || !P)))
+        return -1;
+    if (scheme != ORACLE_FULL_CN && scheme != ORACLE_NUMEROV_SPLIT) return -1;
+    const double complex* psi = (const double complex*)psi_ri;
+    double* x = malloc(sizeof(double) * N);
+    double* V = malloc(sizeof(double) * N);
+    double* dV = malloc(sizeof(double) * N);
+    double* K[3]; double* M[3];
+    for (int k = 0; k < 3; ++k) { K[k] = malloc(sizeof(double) * N); M[k] = malloc(sizeof(double) * N); }
+    double complex* mlo = malloc(sizeof(double complex) * N);
+    double complex* mdi = malloc(sizeof(double complex) * N);
+    double complex* mup = malloc(sizeof(double complex) * N);
+    double complex* lo = malloc(sizeof(double complex) * N);
+    double complex* di = malloc(sizeof(double complex) * N);
+    double complex* up = malloc(sizeof(double complex) * N);
+    double complex* r = malloc(sizeof(double complex) * N);
+    double complex* y = malloc(sizeof(double complex) * N);
+    double complex* work = malloc(sizeof(double complex) * 2 * N);
+    int ok = x && V && dV && mlo && mdi && mup && lo && di && up && r && y && work;
+    for (int k = 0; k < 3; ++k) ok = ok && K[k] && M[k];
+    if (ok) {
+        oracle_grid(N, dx, a, Z, x, V, dV);
+        assemble(N, dx, V, scheme, K[0], K[1], K[2], M[0], M[1], M[2]);
+        for (int j = 0; j < N; ++j) { mlo[j] = M[0][j]; mdi[j] = M[1][j]; mup[j] = M[2][j]; }
+        tri_apply(N, mlo, mdi, mup, psi, r);                         /* M psi */
+        const double norm = 1.0 / (3.14159265358979323846 * eps);   /* N_eps */
+        for (int k = 0; k < n_E; ++k) {
+            const double complex z = E_grid[k] - I * eps;
+            for (int j = 0; j < N; ++j) {
+                lo[j] = z * M[0][j] - K[0][j];
+                di[j] = z * M[1][j] - K[1][j];
+                up[j] = z * M[2][j] - K[2][j];
+            }
+            tri_solve(N, lo, di, up, r, y, work);
+            double s = 0.0;
+            for (int j = 0; j < N; ++j) s += creal(y[j]) * creal(y[j]) + cimag(y[j]) * cimag(y[j]);
+            P[k] = norm * eps * eps * s * dx;
+        }
+    }
+    free(x); free(V); free(dV); free(mlo); free(mdi); free(mup); free(lo); free(di); free(up); free(r); free(y);
+    free(work);
+    for (int k = 0; k < 3; ++k) { free(K[k]); free(M[k]); }
+    return ok ? 0 : -2;
+}

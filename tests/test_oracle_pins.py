@@ -326,3 +326,51 @@ def test_adjoint_matches_central_differences(oracle_mod):
     eps = 1e-6
     fd = (loss(E + eps * v) - loss(E - eps * v)) / (2 * eps)
     assert abs(fd - np.dot(gE, v)) < 1e-6 * abs(fd)
+
+
+# ---------------------------------------------------------------- energy distribution (Sec. 6.1)
+
+def _dense_h0(oracle_mod, N, dx, a, scheme):
+    x, V, _ = oracle_mod.grid(N, dx, a)
+    lap = (np.diag(np.full(N - 1, 1.0), -1) - 2 * np.eye(N) + np.diag(np.full(N - 1, 1.0), 1)) / dx ** 2
+    if scheme == FULL_CN:
+        return -0.5 * lap + np.diag(V)
+    M2 = np.eye(N) + dx ** 2 / 12.0 * lap
+    H = np.linalg.solve(M2, -0.5 * lap) + np.diag(V)   # M2 and lap commute: symmetric
+    return 0.5 * (H + H.T)
+
+
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_energy_distribution_equals_eigen_expansion(oracle_mod, scheme):
+    """P(E) of any state equals its expansion over the eigenpairs (w_k, u_k) of the discrete H0:
+    P(E) = sum_k |<u_k|psi>|^2 (eps/pi) / ((E - w_k)^2 + eps^2) (the resolvent is diagonal in the
+    eigenbasis).  Brute force by dense diagonalisation against the oracle's tridiagonal solves, for
+    an eigenstate (a single Lorentzian) and a random complex state."""
+    rng = np.random.default_rng(23)
+    N, dx, a, eps = 96, 0.25, 1.19, 0.07
+    w, U = eigh(_dense_h0(oracle_mod, N, dx, a, scheme))
+    u = U / np.sqrt(dx)                      # sum |u_k|^2 dx = 1
+    E_grid = np.concatenate([np.linspace(-1.2, 2.0, 40), w[[0, 1, 5]], [w[0] + 0.5 * eps]])
+    states = [u[:, 0].astype(np.complex128), u[:, 3].astype(np.complex128),
+              rng.standard_normal(N) + 1j * rng.standard_normal(N)]
+    for psi in states:
+        c = (u.T @ psi) * dx                 # <u_k|psi> in the sum-dx inner product
+        ref = np.array([np.sum(np.abs(c) ** 2 * (eps / np.pi) / ((E - w) ** 2 + eps ** 2)) for E in E_grid])
+        P = oracle_mod.energy_distribution(psi, E_grid, dx, a, eps, scheme=scheme)
+        assert np.max(np.abs(P - ref) / ref) < 1e-9
+    # an eigenstate at its own energy: the peak of a unit Lorentzian, 1/(pi eps)
+    P0 = oracle_mod.energy_distribution(u[:, 0], [w[0]], dx, a, eps, scheme=scheme)
+    assert abs(P0[0] * np.pi * eps - 1.0) < 1e-9
+
+
+def test_energy_distribution_sum_rule(oracle_mod):
+    """The integral of P over energy is the norm of the state (Sec. 6.1: the integral gives the
+    probability), up to the Lorentzian tails beyond a wide grid."""
+    rng = np.random.default_rng(29)
+    N, dx, a, eps = 80, 0.5, 1.19, 0.05
+    psi = np.exp(-((np.arange(N) - 40.0) * dx) ** 2 / 8 + 0.6j * np.arange(N) * dx) * (1 + 0.2 * rng.standard_normal(N))
+    norm = np.sum(np.abs(psi) ** 2) * dx
+    E_grid = np.linspace(-60.0, 70.0, 26001)
+    P = oracle_mod.energy_distribution(psi, E_grid, dx, a, eps)
+    integral = np.sum(P) * (E_grid[1] - E_grid[0])
+    assert abs(integral / norm - 1.0) < 2e-3
