@@ -54,6 +54,7 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
 
         const GroupDesc G = groups[g];
         const ClassDesc C = cls[G.cls];
+        const Fma64 F{C.one, C.nzero};
         const int N = G.N, Pg = G.P, K = G.K, m = G.m;
         const int64_t slot = G.slot0 + lane;
         const int64_t nt = slot_nt[slot];
@@ -116,8 +117,8 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
 #pragma unroll 2
                 for (int j = lo; j < hi; ++j) {
                     const Cx nx = (j + 2 < N && j + 1 < hi) ? ld_cg(ps + (int64_t)(j + 2) * kLanes + lane) : zero;
-                    const R rr = fma(R(10), pc.x, pm.x + pn.x);
-                    const R ri = fma(R(10), pc.y, pm.y + pn.y);
+                    const R rr = fma(R(10), pc.x, F.add(pm.x, pn.x));
+                    const R ri = fma(R(10), pc.y, F.add(pm.y, pn.y));
                     R wr, wi, lr, li;
                     if constexpr (kMixed) {
                         const float2 fw = __ldg(tF + 3 * j), fl = __ldg(tF + 3 * j + 1);
@@ -126,8 +127,8 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                         const double2 tw = __ldg(tW + j), tl = __ldg(tL + j);
                         wr = tw.x; wi = tw.y; lr = tl.x; li = tl.y;
                     }
-                    const R nr = fma(wr, rr, fma(-wi, ri, fma(-lr, dr, li * di)));
-                    const R ni = fma(wr, ri, fma(wi, rr, fma(-lr, di, -li * dr)));
+                    const R nr = fma(wr, rr, fma(-wi, ri, fma(-lr, dr, F.mul(li, di))));
+                    const R ni = fma(wr, ri, fma(wi, rr, fma(-lr, di, F.mul(-li, dr))));
                     dr = nr;
                     di = ni;
                     r[lane] = mk(dr, di);
@@ -204,11 +205,11 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     const Cx old = ld_cg(ps + (int64_t)j * kLanes + lane);
                     const R tr = fma(R(2), yr, -old.x);
                     const R ti = fma(R(2), yi, -old.y);
-                    R xr = fma(tr, phr, -ti * phi);
-                    R xi = fma(tr, phi, ti * phr);
+                    R xr = fma(tr, phr, F.mul(-ti, phi));
+                    R xi = fma(tr, phi, F.mul(ti, phr));
                     // next point (x smaller by dx): phase times exp(+i dt E dx)
-                    const R qr = fma(phr, wr_, -phi * wi_);
-                    phi = fma(phr, wi_, phi * wr_);
+                    const R qr = fma(phr, wr_, F.mul(-phi, wi_));
+                    phi = fma(phr, wi_, F.mul(phi, wr_));
                     phr = qr;
                     if constexpr (kMixed) {
                         // float copies of (x, dV/dx, m): no double->float conversion per point (on
@@ -233,13 +234,13 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     } else {
                         if (j < jm_lo || j > jm_hi) {
                             const R mm = __ldg(tab_m + j);
-                            xr *= mm;
-                            xi *= mm;
+                            xr = F.mul(xr, mm);
+                            xi = F.mul(xi, mm);
                         }
                         if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
-                        const R rho = fma(xr, xr, xi * xi);
+                        const R rho = fma(xr, xr, F.mul(xi, xi));
                         const double2 xv = __ldg(tab_xv2 + j);
-                        o.n += rho;
+                        o.n = F.add(rho, o.n);
                         o.x = fma(xv.x, rho, o.x);
                         o.v = fma(xv.y, rho, o.v);
                     }
