@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["own", "reference"], default="own")
-    p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large"], default="volume",
+    p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large", "resolvent"], default="volume",
                    help="volume = the benchmark; the others measure the other workloads (one JSON line each)")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                    help="arithmetic of the measured path (the volume benchmark's line is fp64)")
@@ -645,6 +645,43 @@ def other_workload(args):
               dtype="f64" if prec == tdse.TDSE_FP64 else "f32 psi / f64 elimination",
               total_point_steps=wl.point_steps(),
               note="chunks of the first steps_covered steps; field chunks synthesised on the device")
+        return
+
+    if args.workload == "resolvent":
+        # energy distribution (Sec. 6.1) of the volume batch's states after a chunk of the pulse:
+        # 8192 instances x 128 energies, each a complex tridiagonal solve over N = 4096 points
+        wl = inputs.volume_batch()
+        n = wl.n_inst if args.instances <= 0 else min(args.instances, wl.n_inst)
+        N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+        a = softcore.fit_softening(wl.target_energy, N, dx)
+        Nt = 2000 if args.nt <= 0 else args.nt
+        E = torch.empty((n, Nt + 1), dtype=torch.float64, device=dev)
+        inputs.sin2_pulse_batch(Nt, dt, wl.E0[:n], float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi[:n], out=E, xp=torch)
+        E = E.reshape(-1).contiguous()
+        b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent), precision=prec)
+        b.ground_state()
+        d, acc = torch.zeros_like(E), torch.zeros_like(E)
+        b.propagate(E, d, acc)
+        n_E, eps = 128, 0.02
+        E_grid = np.linspace(-0.7, 2.5, n_E)
+        P = torch.empty((n, n_E), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            b.energy_distribution(E_grid, eps, out=P)
+        ts = [timed(lambda: b.energy_distribution(E_grid, eps, out=P)) for _ in range(args.steps)]
+        t = statistics.mean(ts)
+        solves = float(n) * n_E
+        flops = 22.0 * solves * N   # per point: r - a d' 4, times 1/w 6, y = d' - c'y 8, |y|^2 4
+        b.close()
+        peak = FP64_FMA_PER_CLK_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6
+        _line("energy-distribution resolvent solves/s (Sec. 6.1)", solves / t, "tridiagonal solves/s", args,
+              "energy distribution of the volume batch: %d instances x %d energies, N=%d, eps=%g, after %d steps"
+              % (n, n_E, N, eps, Nt),
+              dict(instances=n, energies=n_E, N=N, eps=eps, steps_before=Nt, precision=args.precision),
+              dtype="f64", point_solves_per_s=solves * N / t,
+              roofline={"bound": "alu", "achieved": flops / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                        "frac": flops / t / peak, "traffic": None,
+                        "achieved_how": "22 FP64 flops per point of each (instance, energy) solve; the pivot "
+                                        "pass per (class, energy) is amortised and not counted"})
         return
 
     if args.workload == "adjoint":

@@ -158,6 +158,23 @@ tdse_status tdse_adjoint(tdse_batch* batch, const double* E_dev, const double* g
  * *first_bad_host (may be NULL) receives the first such instance or -1.  Clears the flags. */
 tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream);
 
+/* Time-dependent electron energy distribution of every instance's current state (Sec. 6.1, the
+ * resolvent of the field-free Hamiltonian and its factorised form):
+ *     P_i(E_k) = N_eps eps^2 || (E_k - H0 - i eps)^{-1} psi_i ||^2,  N_eps = 1/(pi eps),
+ * the normalisation of a Lorentzian of half-width eps (an eigenstate of H0 gives a Lorentzian of
+ * unit area times its norm), || v ||^2 = sum_j |v_j|^2 dx.  The inversion is done in the batch
+ * scheme's representation of H0 = M^{-1} K: ((E_k - i eps) M - K)^{-1} (M psi), with M = 1 and the
+ * three-point H0 for FULL_CN, and the Numerov pencil M2, K = -Delta2/2 + M2 V for NUMEROV_SPLIT.
+ * Integrating P over E gives the norm (the ionised part is the integral above the threshold).
+ *   E_grid_host   n_energies energies in a.u. (host, any order, |E| <= 1e12)
+ *   epsilon       resolution eps >= 1e-12 a.u.
+ *   P_dev         out: n_inst x n_energies doubles, row i = instance i in creation order
+ * Works on FP64 and MIXED batches (the solves always run in FP64).  Synchronous: allocates the
+ * pivot tables (2 x 16 B x N x n_energies per class) for the call, keeps a solve scratch of
+ * 8 x SMs x 32 x N_max x 16 B on the batch, and synchronises the stream before returning. */
+tdse_status tdse_energy_distribution(tdse_batch* batch, const double* E_grid_host, int32_t n_energies,
+                                     double epsilon, double* P_dev, void* stream);
+
 /* Power spectrum of sampled signals (Sec. 3.1 / App. A: the source term enters Maxwell's
  * equations through its Fourier transform):
  *     S_i[k] = dt^2 |sum_{n=0}^{L_i - 1} a_i[n] exp(-2 pi i k n / L_i)|^2,  k = k_begin .. k_end - 1,

@@ -104,6 +104,8 @@ struct tdse_batch {
     int64_t* d_slot_row = nullptr;
     int64_t* d_slot_nt = nullptr;
     int64_t* d_slot_valid = nullptr;
+    int64_t* d_slot_group = nullptr;   // group of every slot
+    int64_t* d_slot_inst = nullptr;    // instance of every slot (-1 for padding)
     void* d_psi = nullptr;       // double2 (FP64) or float2 (MIXED) elements
     void* d_scratch = nullptr;
     int* d_busy = nullptr;
@@ -121,6 +123,9 @@ struct tdse_batch {
     void* d_work = nullptr;
     void* d_tape = nullptr;
     int adj_kc = 0, adj_ctas = 0;
+    // energy-distribution buffers (allocated on first use, grown as needed)
+    void* d_ed_scratch = nullptr;
+    int64_t ed_scratch_elems = 0;
     int mixed() const { return precision == TDSE_MIXED ? 1 : 0; }
     size_t cx_bytes() const { return precision == TDSE_MIXED ? sizeof(float2) : sizeof(double2); }
 };
@@ -149,6 +154,12 @@ void free_device(tdse_batch* b)
     cudaFree(b->d_ckpt_off);
     cudaFree(b->d_work);
     cudaFree(b->d_tape);
+    cudaFree(b->d_slot_group);
+    cudaFree(b->d_slot_inst);
+    cudaFree(b->d_ed_scratch);
+    b->d_slot_group = b->d_slot_inst = nullptr;
+    b->d_ed_scratch = nullptr;
+    b->ed_scratch_elems = 0;
     b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
     b->d_ckpt_off = nullptr;
     b->d_cls = nullptr;
@@ -321,10 +332,13 @@ tdse_status build_groups(tdse_batch* b)
     cudaFree(b->d_slot_row);
     cudaFree(b->d_slot_nt);
     cudaFree(b->d_slot_valid);
+    cudaFree(b->d_slot_group);
+    cudaFree(b->d_slot_inst);
     cudaFree(b->d_psi);
     cudaFree(b->d_status);
     cudaFree(b->d_busy);
     cudaFree(b->d_progress);
+    b->d_slot_group = b->d_slot_inst = nullptr;
     b->d_groups = nullptr;
     b->d_slot_row = b->d_slot_nt = b->d_slot_valid = nullptr;
     b->d_psi = nullptr;
@@ -349,6 +363,12 @@ tdse_status build_groups(tdse_batch* b)
     TDSE_CUDA(cudaMemcpy(b->d_slot_row, slot_row.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
     TDSE_CUDA(cudaMemcpy(b->d_slot_nt, slot_nt.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
     TDSE_CUDA(cudaMemcpy(b->d_slot_valid, slot_valid.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
+    std::vector<int64_t> slot_inst(b->n_slots, -1);
+    for (int64_t i = 0; i < n_inst; ++i) slot_inst[b->slot_of_inst[i]] = i;
+    TDSE_CUDA(dev_alloc(&b->d_slot_group, (size_t)b->n_slots), "cudaMalloc(slots)");
+    TDSE_CUDA(dev_alloc(&b->d_slot_inst, (size_t)b->n_slots), "cudaMalloc(slots)");
+    TDSE_CUDA(cudaMemcpy(b->d_slot_group, b->slot_group.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
+    TDSE_CUDA(cudaMemcpy(b->d_slot_inst, slot_inst.data(), sizeof(int64_t) * b->n_slots, cudaMemcpyHostToDevice), "cudaMemcpy(slots)");
     TDSE_CUDA(cudaMemset(b->d_status, 0, sizeof(int) * b->n_slots), "cudaMemset(status)");
     TDSE_CUDA(cudaMemset(b->d_psi, 0, b->cx_bytes() * (size_t)std::max<int64_t>(psi_elems, 1)), "cudaMemset(psi)");
     return TDSE_OK;
@@ -807,6 +827,64 @@ tdse_status tdse_adjoint(tdse_batch* b, const double* E_dev, const double* gd_de
                                      b->d_work, b->d_tape, b->d_scratch, b->rows, n_max, ckpt_every, E_dev, gd_dev,
                                      ga_dev, gE_dev, b->mask_on, b->d_busy, b->d_progress, st),
               "adjoint launch");
+    return TDSE_OK;
+}
+
+tdse_status tdse_energy_distribution(tdse_batch* b, const double* E_grid_host, int32_t n_energies, double epsilon,
+                                     double* P_dev, void* stream)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_energy_distribution: NULL batch");
+    if (n_energies < 0 || n_energies > (1 << 20)) return fail(TDSE_ERR_ARG, "tdse_energy_distribution: n_energies out of [0, 2^20]");
+    if (n_energies > 0 && (!E_grid_host || !P_dev)) return fail(TDSE_ERR_ARG, "tdse_energy_distribution: NULL buffer");
+    if (!is_finite(epsilon) || !(epsilon >= 1e-12)) return fail(TDSE_ERR_ARG, "tdse_energy_distribution: epsilon must be >= 1e-12");
+    for (int k = 0; k < n_energies; ++k)
+        if (!is_finite(E_grid_host[k]) || std::fabs(E_grid_host[k]) > 1e12)
+            return fail(TDSE_ERR_ARG, "tdse_energy_distribution: energy " + std::to_string(k) + " not finite or beyond 1e12");
+    if (!b->initialized) return fail(TDSE_ERR_STATE, "tdse_energy_distribution: no state");
+    if (n_energies == 0) return TDSE_OK;
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_cls = (int)b->classes.size();
+    const int nE_pad = (n_energies + kLanes - 1) / kLanes * kLanes;
+    std::vector<int64_t> piv_off(n_cls);
+    int64_t piv_elems = 0;
+    int n_max = 1;
+    for (int c = 0; c < n_cls; ++c) {
+        piv_off[c] = piv_elems;
+        piv_elems += (int64_t)b->classes[c].N * nE_pad;
+        n_max = std::max(n_max, b->classes[c].N);
+    }
+    const int64_t sc = energy_distribution_scratch_elems(b->sm_count, n_max);
+    if (sc > b->ed_scratch_elems) {
+        TDSE_CUDA(cudaStreamSynchronize(st), "tdse_energy_distribution: synchronize");
+        cudaFree(b->d_ed_scratch);
+        b->d_ed_scratch = nullptr;
+        b->ed_scratch_elems = 0;
+        TDSE_CUDA(cudaMalloc(&b->d_ed_scratch, sizeof(double2) * (size_t)sc), "cudaMalloc(energy distribution scratch)");
+        b->ed_scratch_elems = sc;
+    }
+    // per-call buffers: energies, pivot tables and their offsets (freed after the stream drains)
+    double* d_E = nullptr;
+    void* d_piv = nullptr;
+    int64_t* d_off = nullptr;
+    auto release = [&]() {
+        cudaFree(d_E);
+        cudaFree(d_piv);
+        cudaFree(d_off);
+    };
+    cudaError_t e = cudaMalloc(&d_E, sizeof(double) * n_energies);
+    if (e == cudaSuccess) e = cudaMalloc(&d_piv, sizeof(double2) * 2 * (size_t)piv_elems);
+    if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * n_cls);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_E, E_grid_host, sizeof(double) * n_energies, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, piv_off.data(), sizeof(int64_t) * n_cls, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_energy_distribution(b->mixed(), b->d_groups, b->d_cls, n_cls, b->d_tab, b->d_slot_group,
+                                       b->d_slot_inst, b->n_slots, b->d_psi, d_E, n_energies, epsilon, (int)b->scheme,
+                                       d_piv, d_off, piv_elems, b->d_ed_scratch, n_max, b->sm_count, P_dev, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "tdse_energy_distribution");
     return TDSE_OK;
 }
 

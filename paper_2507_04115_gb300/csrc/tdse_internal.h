@@ -21,6 +21,7 @@ constexpr int kMaxSegments = 16;    // warps per CTA at most (512 threads)
 //            W_j/12 = 1/(12 pivot_j), L_j = A_{j,j-1}/pivot_j, C_j = A_{j,j+1}/pivot_j
 //   nf[3j..3j+2] = the same three factors rounded to float2 (MIXED)
 //   fx[j]  = (x_j, dV_j, m_j, 0) rounded to float4 (MIXED observables and mask)
+//   vv[j]  = V_j                                                          (energy distribution)
 struct ClassDesc {
     int64_t tab_off;      // offset (in doubles) of the class block in the table buffer
     int32_t N;
@@ -54,7 +55,8 @@ __host__ __device__ inline int64_t tab_nl(const ClassDesc& c) { return c.tab_off
 __host__ __device__ inline int64_t tab_nc(const ClassDesc& c) { return c.tab_off + 9 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_nf(const ClassDesc& c) { return c.tab_off + 11 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_fx(const ClassDesc& c) { return c.tab_off + 14 * (int64_t)c.N; }
-inline int64_t tab_doubles(int N) { return 16 * (int64_t)N; }
+__host__ __device__ inline int64_t tab_vv(const ClassDesc& c) { return c.tab_off + 16 * (int64_t)c.N; }
+inline int64_t tab_doubles(int N) { return 17 * (int64_t)N; }
 
 // ---- host-side planning rules shared by the allocating and the static entry points ----
 
@@ -124,6 +126,16 @@ cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, 
                                    void* d_work, void* d_tape, void* d_scratch, int rows, int n_max, int kc,
                                    const double* E, const double* gd, const double* ga, double* gE, int mask_on,
                                    int* d_busy, int* d_progress, cudaStream_t st);
+
+// Energy distribution of every instance state (tdse_resolvent.cu): pivots per (class, energy) into
+// d_piv (2 * piv_elems complex doubles, class c at d_piv_off[c], N_c rows of nE rounded up to 32),
+// then one warp per (instance, 32 energies) with a scratch of energy_distribution_scratch_elems.
+int64_t energy_distribution_scratch_elems(int sm_count, int n_max);
+cudaError_t launch_energy_distribution(int mixed, const GroupDesc* d_groups, const ClassDesc* d_cls, int n_cls,
+                                       const double* d_tab, const int64_t* d_slot_group, const int64_t* d_slot_inst,
+                                       int64_t n_slots, const void* d_psi, const double* d_E_grid, int nE, double eps,
+                                       int scheme, void* d_piv, const int64_t* d_piv_off, int64_t piv_elems,
+                                       void* d_scratch, int n_max, int sm_count, double* P_out, cudaStream_t st);
 
 // Persistent NUMEROV_SPLIT propagation (same scheduler, scratch and layouts; tables nw/nl/nc/nf).
 cudaError_t launch_propagate_numerov(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,

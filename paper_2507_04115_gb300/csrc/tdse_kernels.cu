@@ -54,6 +54,7 @@ __global__ void k_build_tables(const ClassDesc* cls, int n_cls, double dt, doubl
         }
         mk[j] = m;
         reinterpret_cast<float4*>(tab + tab_fx(C))[j] = make_float4((float)x, (float)dV, (float)m, 0.0f);
+        tab[tab_vv(C) + j] = V;
     }
 }
 

@@ -21,7 +21,7 @@ _lib = None
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
-           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_last_error")
+           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(path: str | None = None):
     L.tdse_autotune.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.POINTER(tdse_tune_trial), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp]
     L.tdse_set_layout.argtypes = [_vp, ctypes.c_int32]
+    L.tdse_energy_distribution.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -246,6 +247,17 @@ class Batch:
                     warps_per_cta=info.warps_per_cta, ctas=info.ctas, slice_steps=info.slice_steps,
                     scratch_bytes=info.scratch_bytes, psi_bytes=info.psi_bytes,
                     lanes_per_instance=info.lanes_per_instance)
+
+    def energy_distribution(self, E_grid, epsilon, out=None, stream=None):
+        """P[i, k]: energy distribution of instance i's current state at E_grid[k] with resolution
+        epsilon (see tdse_energy_distribution); returns a float64 device tensor n_inst x len(E_grid)."""
+        import torch
+        Eg = np.ascontiguousarray(E_grid, dtype=np.float64)
+        if out is None:
+            out = torch.empty((self.n_inst, Eg.size), dtype=torch.float64, device=torch.device("cuda", self.device))
+        _check(load().tdse_energy_distribution(self._h, Eg.ctypes.data_as(_dp), int(Eg.size), float(epsilon),
+                                               _dev_ptr(out, "P"), _stream_ptr(stream)))
+        return out
 
     def set_layout(self, lanes_per_instance=0):
         """Lanes per instance of the layout (see tdse_set_layout; 0 = cost model).  Discards the state."""

@@ -72,6 +72,7 @@ def test_null_handles_are_rejected(lib):
     n = ctypes.c_int32(-1)
     assert lib.tdse_autotune(None, None, None, None, 0, 0, 4, 1, None, 0, ctypes.byref(n), None) == tdse.TDSE_ERR_ARG
     assert n.value == -1
+    assert lib.tdse_energy_distribution(None, None, 4, 0.05, None, None) == tdse.TDSE_ERR_ARG
     lib.tdse_batch_destroy(None)
 
 
