@@ -60,7 +60,7 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=2, help="chunks timed end to end through host buffers")
     p.add_argument("--cpu-baseline", type=int, default=1, help="time the oracle on the host cores (rank 0, N = 1)")
     p.add_argument("--cpu-instances", type=int, default=0, help="oracle sample size (0 = one per core, max 16)")
-    p.add_argument("--ref-steps-per-step", type=int, default=8192, help="oracle time steps per reference step")
+    p.add_argument("--ref-steps-per-step", type=int, default=4096, help="oracle time steps per reference step")
     p.add_argument("--warps", type=int, default=0, help="override warps per CTA (segments per instance)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="override CTAs per SM of the persistent grid")
     p.add_argument("--slice", type=int, default=0, help="override time steps per scheduling slice")
@@ -135,7 +135,7 @@ def kernel_source_sha():
 
 
 def kernel_traffic_per_point_step():
-    """DRAM bytes per grid-point step of k_propagate_fp64 from the committed ncu summary, or None
+    """DRAM bytes per grid-point step of k_propagate_full_cn<fp64> from the committed ncu summary, or None
     when the summary is missing or the kernel source changed since the capture."""
     if not os.path.exists(TRAFFIC_FILE):
         return None

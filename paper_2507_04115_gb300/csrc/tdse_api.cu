@@ -94,7 +94,7 @@ struct tdse_batch {
     int lanes_request = 0;             // tdse_set_layout's lanes per instance (0 = cost model)
     // launch configuration of the persistent propagation kernel
     int warps_override = 0, ctas_per_sm_override = 0, slice_override = 0, max_ctas_override = 0;
-    int warps = 8, ctas = 0, rows = 0, slice = 16;
+    int warps = 8, ctas = 0, rows = 0, slice = 16, ring = 4;
     int sm_count = 0;
     bool initialized = false;
     // device memory
@@ -405,6 +405,7 @@ tdse_status build_plan(tdse_batch* b)
     b->rows = rows;
     const int per_sm_max = propagate_max_ctas_per_sm(b->mixed(), b->warps);
     const int per_sm = b->ctas_per_sm_override > 0 ? std::min(b->ctas_per_sm_override, per_sm_max) : 1;
+    b->ring = propagate_ring_slots(b->warps, per_sm);
     b->ctas = (int)std::min<int64_t>((int64_t)b->groups.size(), (int64_t)b->sm_count * per_sm);
     if (b->max_ctas_override > 0) b->ctas = std::min(b->ctas, b->max_ctas_override);
     const int64_t sc = (int64_t)b->ctas * b->warps * rows * 2 * kLanes;
@@ -692,7 +693,7 @@ tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, do
         TDSE_CUDA(launch_propagate_full_cn(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas,
                                            b->d_cls, b->d_tab, b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_scratch,
                                            b->rows, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, b->slice,
-                                           b->mask_on, b->d_busy, b->d_progress, b->d_status, st),
+                                           b->mask_on, b->d_busy, b->d_progress, b->d_status, b->ring, st),
                   "propagate launch");
     return TDSE_OK;
 }

@@ -189,7 +189,7 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     const int64_t* __restrict__ slot_nt, void* __restrict__ psi_raw, void* __restrict__ scratch_raw,
                     int rows, const double* __restrict__ E, double* __restrict__ d_out, double* __restrict__ a_out,
                     int64_t sample_base, int64_t step_begin, int64_t step_end, int slice, int mask_on,
-                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status)
+                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status, int ring_slots)
 {
     using R = typename Prec<kMixed>::R;
     using Cx = typename Prec<kMixed>::C;
@@ -201,7 +201,7 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
     Cx* __restrict__ psi_all = static_cast<Cx*>(psi_raw);
     Cx* __restrict__ sc = static_cast<Cx*>(scratch_raw) + ((int64_t)blockIdx.x * P + w) * rows * (2 * kLanes);
     // MIXED: per-warp ring of bulk-copy slots after the reduction area (see the back substitution)
-    const int kRing = full_cn_ring_slots(P);
+    const int kRing = ring_slots;   // bulk-copy slots per warp (MIXED)
     uint64_t* bars = reinterpret_cast<uint64_t*>(red + P * 3 * kLanes) + w * kRing;
     unsigned char* ring = reinterpret_cast<unsigned char*>(reinterpret_cast<uint64_t*>(red + P * 3 * kLanes) + P * kRing) +
                           (size_t)w * kRing * kSlotBytes;
@@ -523,14 +523,15 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
                                      const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
                                      const double* E, double* d_out, double* a_out, int64_t sample_base,
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
-                                     int* d_progress, int* d_status, cudaStream_t st)
+                                     int* d_progress, int* d_status, int ring, cudaStream_t st)
 {
     if (n_groups == 0 || ctas == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(d_busy, 0, sizeof(int) * n_groups, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d_progress, 0, sizeof(int) * n_groups, st);
     if (e != cudaSuccess) return e;
-    const size_t smem = full_cn_smem_bytes(mixed, P);
+    if (mixed && (ring < kMinRing || ring > kMaxRing)) return cudaErrorInvalidValue;
+    const size_t smem = full_cn_smem_bytes(mixed, P, ring);
     if (mixed) {
         static bool attr_set = false;
         if (!attr_set) {
@@ -541,19 +542,21 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
         }
         k_propagate_full_cn<true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
-            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status);
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring);
     } else {
         k_propagate_full_cn<false><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
-            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status);
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring);
     }
     return cudaGetLastError();
 }
 
+int propagate_ring_slots(int P, int per_sm) { return full_cn_ring_slots(P, per_sm); }
+
 int propagate_max_ctas_per_sm(int mixed, int P)
 {
     int n = 0;
-    const size_t smem = full_cn_smem_bytes(mixed, P);
+    const size_t smem = full_cn_smem_bytes(mixed, P, kMinRing);   // the shallowest ring
     if (mixed &&
         cudaFuncSetAttribute(k_propagate_full_cn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)full_cn_smem_max_bytes()) != cudaSuccess) {

@@ -61,7 +61,7 @@ inline int64_t tab_doubles(int N) { return 17 * (int64_t)N; }
 // ---- host-side planning rules shared by the allocating and the static entry points ----
 
 // Halo length K such that beta^K < 1e-18: the truncated sweeps then agree with the exact Thomas
-// solve below double rounding (|gamma| <= |beta| per point, see tdse_propagate.cu); 0 when beta is
+// solve below double rounding (|gamma| <= |beta| per point, see tdse_full_cn.cu); 0 when beta is
 // too close to 1 for truncation to pay off.
 inline int halo_for_beta(double beta)
 {
@@ -106,16 +106,20 @@ cudaError_t launch_broadcast_psi(int mixed, const GroupDesc* d_groups, int64_t n
                                  const int64_t* d_work_off, const int64_t* d_slot_valid, void* d_psi,
                                  cudaStream_t st);
 
-// Persistent FULL_CN propagation (tdse_propagate.cu): `ctas` CTAs of P warps pick groups
+// Persistent FULL_CN propagation (tdse_full_cn.cu): `ctas` CTAs of P warps pick groups
 // dynamically, `slice` steps at a time.  mixed = 0: psi and scratch are double2; mixed = 1:
-// float2.  Scratch holds ctas * P * rows rows of 2 * 32 complex values.
+// float2.  Scratch holds ctas * P * rows rows of 2 * 32 complex values.  ring: MIXED bulk-copy
+// slots per warp in [2, 4] (full_cn_ring_slots for the CTAs per SM of the launch).
 cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
                                      const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
                                      const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
                                      const double* E, double* d_out, double* a_out, int64_t sample_base,
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
-                                     int* d_progress, int* d_status, cudaStream_t st);
+                                     int* d_progress, int* d_status, int ring, cudaStream_t st);
+// CTAs of P warps that fit on one SM (MIXED: with the shallowest bulk-copy ring).
 int propagate_max_ctas_per_sm(int mixed, int P);
+// MIXED bulk-copy slots per warp when per_sm CTAs of P warps share an SM.
+int propagate_ring_slots(int P, int per_sm);
 
 // Discrete adjoint of FULL_CN in FP64 (tdse_adjoint.cu): one CTA per group for the whole call.
 // lam: psi-shaped; ckpt: per group (intervals + 1) states at ckpt_off[g]; work: ctas * n_max * 32;

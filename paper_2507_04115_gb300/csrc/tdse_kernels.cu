@@ -1,6 +1,7 @@
 // Set-up and auxiliary kernels of libtdse (sm_103a): per-class tables, imaginary-time ground
 // state, wavefunction broadcast and access, and the DFT power spectrum.  The propagation kernels
-// live in tdse_propagate.cu.
+// live in tdse_full_cn.cu and tdse_numerov.cu, the adjoint in tdse_adjoint.cu, the energy
+// distribution in tdse_resolvent.cu.
 #include "tdse_device.cuh"
 #include "tdse_internal.h"
 

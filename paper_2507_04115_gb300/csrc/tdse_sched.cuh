@@ -9,33 +9,38 @@ namespace tdse {
 
 // MIXED back substitution streams its rows through a per-warp ring of shared-memory slots, each
 // holding kSlotRows rows (512-byte float2 gamma|D scratch rows, then 256-byte float2 psi rows):
-// 4 slots per warp when they fit in 220 KB, at least 2.
+// as many slots per warp (2 to 4) as fit when `per_sm` CTAs share an SM's 220 KB.  Several CTAs per
+// SM let the FP64-heavy forward sweep of one group overlap the float back substitution of another
+// (each CTA synchronises only its own warps).
 constexpr int kSlotRows = 8;
 constexpr int kSlotBytes = kSlotRows * 768;
 constexpr int kMaxRing = 4;
+constexpr int kMinRing = 2;
 
-__host__ __device__ inline int full_cn_ring_slots(int P)
+inline int full_cn_ring_slots(int P, int per_sm)
 {
     const long red = (long)P * 3 * 32 * 8;
-    const long r = (220L * 1024 - red) / ((long)P * (kSlotBytes + 8));
-    return r < 2 ? 2 : (r > kMaxRing ? kMaxRing : (int)r);
+    const long r = (220L * 1024 / (per_sm < 1 ? 1 : per_sm) - red) / ((long)P * (kSlotBytes + 8));
+    return r < kMinRing ? kMinRing : (r > kMaxRing ? kMaxRing : (int)r);
 }
 
-__host__ __device__ inline size_t full_cn_smem_bytes(int mixed, int P)
+__host__ __device__ inline size_t full_cn_smem_bytes(int mixed, int P, int ring)
 {
     size_t b = (size_t)P * 3 * 32 * sizeof(double);
-    if (mixed) b += (size_t)P * full_cn_ring_slots(P) * (sizeof(uint64_t) + kSlotBytes);
+    if (mixed) b += (size_t)P * ring * (sizeof(uint64_t) + kSlotBytes);
     return b;
 }
 
-// Largest dynamic shared memory the MIXED kernel asks for (over 1..16 warps).
+// Largest dynamic shared memory the MIXED kernel asks for (over 1..16 warps, one CTA per SM).
 inline size_t full_cn_smem_max_bytes()
 {
     size_t m = 0;
-    for (int P = 1; P <= 16; ++P) m = full_cn_smem_bytes(1, P) > m ? full_cn_smem_bytes(1, P) : m;
+    for (int P = 1; P <= 16; ++P) {
+        const size_t b = full_cn_smem_bytes(1, P, full_cn_ring_slots(P, 1));
+        m = b > m ? b : m;
+    }
     return m;
 }
-
 
 // Storage and arithmetic types per precision: FP64 keeps everything in double; MIXED keeps psi,
 // the solve's right-hand side and back substitution, and the pointwise update in float, while the
