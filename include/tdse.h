@@ -227,6 +227,15 @@ tdse_status tdse_set_layout(tdse_batch* batch, int32_t lanes_per_instance);
 tdse_status tdse_set_launch(tdse_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
                             int32_t max_ctas);
 
+/* Bound on the MIXED kernels' waits for their bulk copies (global -> shared memory), in mbarrier
+ * polls; default 2^22 (a copy lands within microseconds).  A wait that runs out drains the copies
+ * still in flight (with the default bound), stops using bulk copies for the rest of the launch and
+ * flags the group's instances, so tdse_check then returns TDSE_ERR_TIMEOUT; the results of that
+ * launch are invalid but the context stays usable.  polls = 0 makes every wait give up at once:
+ * the test of this path (there is no way to make a real copy fail without faulting the GPU).
+ * The paper has no counterpart.  Applies to later calls; polls in [0, 2^30]. */
+tdse_status tdse_set_wait_limit(tdse_batch* batch, int64_t polls);
+
 /* Launch-shape autotuner.  The paper runs one solver per MPI rank and has no counterpart; this
  * picks, by timing, the shape tdse_set_launch sets: warps per CTA (also the number of segments
  * each instance's tridiagonal solve is split into, i.e. the depth of the parallel split), CTAs per

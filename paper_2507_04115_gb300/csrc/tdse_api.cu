@@ -95,6 +95,7 @@ struct tdse_batch {
     // launch configuration of the persistent propagation kernel
     int warps_override = 0, ctas_per_sm_override = 0, slice_override = 0, max_ctas_override = 0;
     int warps = 8, ctas = 0, rows = 0, slice = 16, ring = 4;
+    uint32_t wait_polls = 1u << 22;   // MIXED bulk-copy wait bound (tdse_set_wait_limit)
     int sm_count = 0;
     bool initialized = false;
     // device memory
@@ -597,6 +598,14 @@ tdse_status tdse_plan(const tdse_batch* b, tdse_plan_info* info)
     return TDSE_OK;
 }
 
+tdse_status tdse_set_wait_limit(tdse_batch* b, int64_t polls)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_set_wait_limit: NULL batch");
+    if (polls < 0 || polls > (int64_t(1) << 30)) return fail(TDSE_ERR_ARG, "tdse_set_wait_limit: polls out of [0, 2^30]");
+    b->wait_polls = (uint32_t)polls;
+    return TDSE_OK;
+}
+
 tdse_status tdse_set_layout(tdse_batch* b, int32_t lanes_per_instance)
 {
     if (!b) return fail(TDSE_ERR_ARG, "tdse_set_layout: NULL batch");
@@ -693,7 +702,7 @@ tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, do
         TDSE_CUDA(launch_propagate_full_cn(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas,
                                            b->d_cls, b->d_tab, b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_scratch,
                                            b->rows, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, b->slice,
-                                           b->mask_on, b->d_busy, b->d_progress, b->d_status, b->ring, st),
+                                           b->mask_on, b->d_busy, b->d_progress, b->d_status, b->ring, b->wait_polls, st),
                   "propagate launch");
     return TDSE_OK;
 }

@@ -189,7 +189,7 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     const int64_t* __restrict__ slot_nt, void* __restrict__ psi_raw, void* __restrict__ scratch_raw,
                     int rows, const double* __restrict__ E, double* __restrict__ d_out, double* __restrict__ a_out,
                     int64_t sample_base, int64_t step_begin, int64_t step_end, int slice, int mask_on,
-                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status, int ring_slots)
+                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status, int ring_slots, uint32_t wait_polls)
 {
     using R = typename Prec<kMixed>::R;
     using Cx = typename Prec<kMixed>::C;
@@ -377,11 +377,13 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 int blk = 0;
                 for (int b = 0; b < nblk && !timed_out; ++b) {
                     const uint32_t k = (rc + b) % kRing;
-                    const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + k, ((rc + b) / kRing) & 1u, 1u << 22));
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait(bars + k, ((rc + b) / kRing) & 1u, wait_polls));
                     if (!ok) {
+                        // drain every copy still in flight (this slot's included) with the full
+                        // bound before leaving the ring unused for the rest of the launch
                         timed_out = true;
-                        for (int b2 = b + 1; b2 < issued; ++b2)
-                            mbar_wait(bars + (rc + b2) % kRing, ((rc + b2) / kRing) & 1u, 1u << 22);
+                        for (int b2 = b; b2 < issued; ++b2)
+                            mbar_wait(bars + (rc + b2) % kRing, ((rc + b2) / kRing) & 1u, kDrainPolls);
                         break;
                     }
                     const unsigned char* slotp = ring + k * kSlotBytes;
@@ -523,7 +525,7 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
                                      const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
                                      const double* E, double* d_out, double* a_out, int64_t sample_base,
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
-                                     int* d_progress, int* d_status, int ring, cudaStream_t st)
+                                     int* d_progress, int* d_status, int ring, uint32_t wait_polls, cudaStream_t st)
 {
     if (n_groups == 0 || ctas == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(d_busy, 0, sizeof(int) * n_groups, st);
@@ -542,11 +544,11 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
         }
         k_propagate_full_cn<true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
-            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring);
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring, wait_polls);
     } else {
         k_propagate_full_cn<false><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
-            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring);
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring, wait_polls);
     }
     return cudaGetLastError();
 }

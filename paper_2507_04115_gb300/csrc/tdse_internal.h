@@ -109,13 +109,15 @@ cudaError_t launch_broadcast_psi(int mixed, const GroupDesc* d_groups, int64_t n
 // Persistent FULL_CN propagation (tdse_full_cn.cu): `ctas` CTAs of P warps pick groups
 // dynamically, `slice` steps at a time.  mixed = 0: psi and scratch are double2; mixed = 1:
 // float2.  Scratch holds ctas * P * rows rows of 2 * 32 complex values.  ring: MIXED bulk-copy
-// slots per warp in [2, 4] (full_cn_ring_slots for the CTAs per SM of the launch).
+// slots per warp in [2, 4] (full_cn_ring_slots for the CTAs per SM of the launch); wait_polls:
+// polls before a MIXED bulk-copy wait gives up (the batch reports TDSE_ERR_TIMEOUT).
 cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
                                      const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
                                      const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
                                      const double* E, double* d_out, double* a_out, int64_t sample_base,
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
-                                     int* d_progress, int* d_status, int ring, cudaStream_t st);
+                                     int* d_progress, int* d_status, int ring, uint32_t wait_polls,
+                                     cudaStream_t st);
 // CTAs of P warps that fit on one SM (MIXED: with the shallowest bulk-copy ring).
 int propagate_max_ctas_per_sm(int mixed, int P);
 // MIXED bulk-copy slots per warp when per_sm CTAs of P warps share an SM.

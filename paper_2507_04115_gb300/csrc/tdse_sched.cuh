@@ -16,6 +16,11 @@ constexpr int kSlotRows = 8;
 constexpr int kSlotBytes = kSlotRows * 768;
 constexpr int kMaxRing = 4;
 constexpr int kMinRing = 2;
+// Polls of an mbarrier before a bulk-copy wait gives up (a copy of a few hundred bytes lands in
+// microseconds; 2^22 polls is far beyond that), and the same bound for draining copies in flight
+// after a wait gave up.
+constexpr uint32_t kWaitPolls = 1u << 22;
+constexpr uint32_t kDrainPolls = 1u << 22;
 
 inline int full_cn_ring_slots(int P, int per_sm)
 {

@@ -193,7 +193,7 @@ extern "C" tdse_status tdse_propagate_static(const tdse_instance* inst_host, int
     if (e == cudaSuccess)
         e = launch_propagate_full_cn(0, d_groups, n_groups, warps, ctas, d_cls, d_tab, d_row, d_nt, psi_dev, d_scratch,
                                      rows, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, 16, mask_on, d_busy,
-                                     d_prog, d_status, 2 /* bulk-copy ring: MIXED only */, s);
+                                     d_prog, d_status, 2 /* bulk-copy ring: MIXED only */, 1u << 22, s);
     if (e != cudaSuccess) {
         static thread_local char msg[256];
         std::snprintf(msg, sizeof msg, "tdse_propagate_static: %s", cudaGetErrorString(e));

@@ -21,7 +21,7 @@ _lib = None
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
-           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_last_error")
+           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(path: str | None = None):
     L.tdse_autotune.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.POINTER(tdse_tune_trial), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp]
     L.tdse_set_layout.argtypes = [_vp, ctypes.c_int32]
+    L.tdse_set_wait_limit.argtypes = [_vp, ctypes.c_int64]
     L.tdse_energy_distribution.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
@@ -258,6 +259,10 @@ class Batch:
         _check(load().tdse_energy_distribution(self._h, Eg.ctypes.data_as(_dp), int(Eg.size), float(epsilon),
                                                _dev_ptr(out, "P"), _stream_ptr(stream)))
         return out
+
+    def set_wait_limit(self, polls=1 << 22):
+        """Bound of the MIXED bulk-copy waits in polls (see tdse_set_wait_limit; 0 = give up at once)."""
+        _check(load().tdse_set_wait_limit(self._h, int(polls)))
 
     def set_layout(self, lanes_per_instance=0):
         """Lanes per instance of the layout (see tdse_set_layout; 0 = cost model).  Discards the state."""

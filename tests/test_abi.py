@@ -73,6 +73,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.tdse_autotune(None, None, None, None, 0, 0, 4, 1, None, 0, ctypes.byref(n), None) == tdse.TDSE_ERR_ARG
     assert n.value == -1
     assert lib.tdse_energy_distribution(None, None, 4, 0.05, None, None) == tdse.TDSE_ERR_ARG
+    assert lib.tdse_set_wait_limit(None, 10) == tdse.TDSE_ERR_ARG
     lib.tdse_batch_destroy(None)
 
 

@@ -637,3 +637,37 @@ def test_lane_split_matches_32_wide(env):
             sl = slice(offs[i], offs[i + 1])
             assert _rel(outs[lanes][0][sl], outs[1][0][sl]) < 1e-11, (lanes, i)
             assert _rel(outs[lanes][1][sl], outs[1][1][sl]) < 1e-11, (lanes, i)
+
+
+# ------------------------------------------------------------------------------- failure detection
+
+def test_bulk_copy_wait_timeout_is_reported_and_context_survives(env):
+    """A MIXED bulk-copy wait that gives up (forced with a zero poll bound: no copy can be made to
+    fail without faulting the GPU) drains the copies in flight, flags the instances, and tdse_check
+    reports TDSE_ERR_TIMEOUT; the next propagation with the normal bound is correct again."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    n, N, dx, a, dt, nt = 40, 512, 0.2, 1.19, 0.05, 120
+    E = inputs.sin2_pulse(nt, dt, 0.06, 0.057, 1.0, 0.0)
+    Et = torch.from_numpy(np.tile(E, n)).to("cuda")
+    b = tdse.Batch([N] * n, dx, a, [nt] * n, dt, absorber=(20.0, 0.125), precision=tdse.TDSE_MIXED,
+                   lanes_per_instance=1)
+    b.ground_state(**GS_KW)
+    d, acc = torch.zeros_like(Et), torch.zeros_like(Et)
+    b.set_wait_limit(0)
+    b.propagate(Et, d, acc)
+    with pytest.raises(tdse.TDSEError) as ei:
+        b.check()
+    assert ei.value.status == tdse.TDSE_ERR_TIMEOUT
+    b.set_wait_limit()
+    b.ground_state(**GS_KW)
+    b.propagate(Et, d, acc)
+    torch.cuda.synchronize()
+    assert b.check() == -1
+    psi0, _, _ = oracle.ground_state(N, dx, a, **GS_KW)
+    m = oracle.mask(N, dx, 20.0, 0.125)
+    _, d_o, a_o = oracle.propagate(psi0, E, dx, dt, a, mask_values=m)
+    ah = acc.cpu().numpy()
+    for i in (0, n - 1):
+        assert _rel(ah[i * (nt + 1):(i + 1) * (nt + 1)], a_o) < MIXED_SERIES
+    b.close()
