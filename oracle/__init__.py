@@ -19,6 +19,9 @@ with respect to every field sample).
 ``energy_distribution``: the time-dependent electron energy distribution P(E) of a state through the
 resolvent of the field-free Hamiltonian (Sec. 6.1).
 
+``resample_field``: the input step of Sec. 4.2, a coarsely sampled field moved to t = 0 and
+interpolated to the propagation step by zero-padding its DFT.
+
 Scheme ids: 0 = FULL_CN (E in the diagonal at the midpoint field), 1 = NUMEROV_SPLIT
 (the paper's Eqs. "CN - step 4/2/3").
 """
@@ -164,6 +167,29 @@ def energy_distribution(psi, E_grid, dx, a, eps, Z=1.0, scheme=FULL_CN):
     _check(lib().oracle_energy_distribution(psi.size, dx, a, Z, scheme, psi.view(np.float64).ctypes.data_as(_dp),
                                             _ptr(Eg), Eg.size, eps, _ptr(P)), "oracle_energy_distribution")
     return P
+
+
+def resample_field(coarse, dt_coarse, dt_fine, n_fine):
+    """Field ingestion (Sec. 4.2): the coarse samples E(t_min + m dt_coarse), m = 0..M-1, moved to the
+    time origin t = 0 and interpolated to t_n = n dt_fine, n = 0..n_fine-1, by zero-padding the DFT:
+        E(t) = (1/M) sum_{k=-floor(M/2)}^{floor(M/2)} w_k Ehat_k exp(2 pi i k t / T),  T = M dt_coarse,
+    Ehat = DFT of the samples (numpy's FFT as the library primitive), w_k = 1/2 for |k| = M/2 (even M,
+    the Nyquist bin split between the two ends of the padded spectrum), otherwise 1."""
+    c = np.asarray(coarse, dtype=np.float64)
+    M = c.size
+    Eh = np.fft.fft(c)
+    k = np.arange(-(M // 2), M // 2 + 1)
+    w = np.ones(k.size)
+    if M % 2 == 0:
+        w[0] = w[-1] = 0.5
+    coef = w * Eh[k % M] / M
+    t = np.arange(n_fine) * dt_fine
+    T = M * dt_coarse
+    out = np.empty(n_fine)
+    for s0 in range(0, n_fine, 4096):   # bounded memory for the explicit sum
+        tt = t[s0:s0 + 4096]
+        out[s0:s0 + 4096] = np.real(np.exp(2j * np.pi * np.outer(tt, k) / T) @ coef)
+    return out
 
 
 def spectrum(acc, dt):

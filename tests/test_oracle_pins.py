@@ -374,3 +374,46 @@ def test_energy_distribution_sum_rule(oracle_mod):
     P = oracle_mod.energy_distribution(psi, E_grid, dx, a, eps)
     integral = np.sum(P) * (E_grid[1] - E_grid[0])
     assert abs(integral / norm - 1.0) < 2e-3
+
+
+# ---------------------------------------------------------------- field ingestion (Sec. 4.2)
+
+def test_resampling_is_exact_at_coarse_samples_and_for_band_limited_fields(oracle_mod):
+    """Zero-padding the DFT is the trigonometric interpolant: it passes through every coarse sample,
+    and a field made of harmonics of the window below the Nyquist frequency comes back exactly at
+    every fine time (odd and even numbers of samples)."""
+    rng = np.random.default_rng(31)
+    for M in (64, 75):
+        dtc, r = 0.4, 8
+        T = M * dtc
+        c = rng.standard_normal(M)
+        fine = oracle_mod.resample_field(c, dtc, dtc / r, M * r)
+        assert np.max(np.abs(fine[::r] - c)) < 1e-12
+        tm = np.arange(M) * dtc
+        f = lambda t: 0.3 + np.cos(2 * np.pi * 3 * t / T) + 0.5 * np.sin(2 * np.pi * 7 * t / T + 0.3)
+        tf = np.arange(M * r) * dtc / r
+        got = oracle_mod.resample_field(f(tm), dtc, dtc / r, M * r)
+        assert np.max(np.abs(got - f(tf))) < 1e-12
+
+
+def test_resampling_equals_zero_padded_inverse_fft(oracle_mod):
+    """When the window holds a whole number L of fine steps, the interpolant equals the inverse FFT
+    of the spectrum zero-padded to L bins (Nyquist bin split in two), times L / M."""
+    rng = np.random.default_rng(37)
+    for M, L in ((64, 512), (75, 600)):
+        dtc = 0.4
+        c = rng.standard_normal(M)
+        Eh = np.fft.fft(c)
+        pad = np.zeros(L, dtype=np.complex128)
+        h = M // 2
+        if M % 2 == 0:
+            pad[:h] = Eh[:h]
+            pad[h] = 0.5 * Eh[h]
+            pad[L - h] = 0.5 * Eh[h]
+            pad[L - h + 1:] = Eh[h + 1:]
+        else:
+            pad[:h + 1] = Eh[:h + 1]
+            pad[L - h:] = Eh[h + 1:]
+        ref = np.real(np.fft.ifft(pad)) * L / M
+        got = oracle_mod.resample_field(c, dtc, M * dtc / L, L)
+        assert np.max(np.abs(got - ref)) < 1e-12
