@@ -53,7 +53,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["own", "reference"], default="own")
-    p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large", "resolvent"], default="volume",
+    p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large", "resolvent", "field"],
+                   default="volume",
                    help="volume = the benchmark; the others measure the other workloads (one JSON line each)")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                    help="arithmetic of the measured path (the volume benchmark's line is fp64)")
@@ -645,6 +646,28 @@ def other_workload(args):
               dtype="f64" if prec == tdse.TDSE_FP64 else "f32 psi / f64 elimination",
               total_point_steps=wl.point_steps(),
               note="chunks of the first steps_covered steps; field chunks synthesised on the device")
+        return
+
+    if args.workload == "field":
+        # field ingestion (Sec. 4.2): 8192 coarse rows of 2400 samples at 0.5 a.u. (a 1200 a.u. window
+        # around the 10-cycle pulse) interpolated to the volume batch's 55160 samples at dt = 0.02
+        wl = inputs.volume_batch()
+        n = wl.n_inst if args.instances <= 0 else min(args.instances, wl.n_inst)
+        M, dt_c, dt_f = 2400, 0.5, wl.dt
+        n_fine = int(wl.n_steps[0]) + 1
+        coarse = torch.empty((n, M - 1), dtype=torch.float64, device=dev)
+        inputs.sin2_pulse_batch(M - 2, dt_c, wl.E0[:n], float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi[:n],
+                                out=coarse, xp=torch)
+        coarse = torch.cat([coarse, torch.zeros((n, 1), dtype=torch.float64, device=dev)], dim=1).contiguous()
+        out = torch.empty((n, n_fine), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            tdse.resample_field(coarse, dt_c, dt_f, n_fine, out=out)
+        ts = [timed(lambda: tdse.resample_field(coarse, dt_c, dt_f, n_fine, out=out)) for _ in range(args.steps)]
+        t = statistics.mean(ts)
+        _line("field ingestion samples/s (Sec. 4.2, zero-padded DFT interpolation)", float(n) * n_fine / t,
+              "fine samples/s", args, "%d rows x %d coarse samples (dt %g) -> %d samples (dt %g)" % (n, M, dt_c, n_fine, dt_f),
+              dict(rows=n, M=M, dt_coarse=dt_c, dt_fine=dt_f, n_fine=n_fine), dtype="f64",
+              flops_per_sample=6 * (M // 2 + 1), seconds_per_call=t)
         return
 
     if args.workload == "resolvent":

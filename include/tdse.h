@@ -175,6 +175,21 @@ tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream)
 tdse_status tdse_energy_distribution(tdse_batch* batch, const double* E_grid_host, int32_t n_energies,
                                      double epsilon, double* P_dev, void* stream);
 
+/* Field ingestion (Sec. 4.2: the input interval is shifted to start at t = 0 and the coarsely
+ * sampled field is interpolated to the propagation step by zero-padding in the Fourier domain).
+ * Row r of coarse_dev holds M samples E(t_min + m dt_coarse), m = 0..M-1 (rows contiguous, M
+ * apart); row r of out_dev (at r * out_stride) receives n_fine samples at t = n dt_fine, t measured
+ * from the row's first sample:
+ *     E(t) = (1/M) sum_{k=-floor(M/2)}^{floor(M/2)} w_k Ehat_k exp(2 pi i k t / T),  T = M dt_coarse,
+ * Ehat the DFT of the row, w_k = 1/2 for |k| = M/2 (even M: the Nyquist bin split between the two
+ * ends of the padded spectrum), else 1 -- the trigonometric interpolant, which reproduces the coarse
+ * samples exactly.  It is T-periodic: times beyond the window wrap around, so pad the coarse row
+ * with zeros past the pulse.  With out_stride equal to a batch's row stride the output feeds
+ * tdse_propagate directly.  M in [2, 8192]; computed in FP64; synchronous (allocates
+ * n_rows x (M/2+1) x 16 bytes for the call). */
+tdse_status tdse_resample_field(const double* coarse_dev, int64_t n_rows, int32_t M, double dt_coarse, double dt_fine,
+                                int64_t n_fine, int64_t out_stride, double* out_dev, int device, void* stream);
+
 /* Power spectrum of sampled signals (Sec. 3.1 / App. A: the source term enters Maxwell's
  * equations through its Fourier transform):
  *     S_i[k] = dt^2 |sum_{n=0}^{L_i - 1} a_i[n] exp(-2 pi i k n / L_i)|^2,  k = k_begin .. k_end - 1,

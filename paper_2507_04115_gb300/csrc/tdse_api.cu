@@ -898,6 +898,31 @@ tdse_status tdse_energy_distribution(tdse_batch* b, const double* E_grid_host, i
     return TDSE_OK;
 }
 
+tdse_status tdse_resample_field(const double* coarse_dev, int64_t n_rows, int32_t M, double dt_coarse, double dt_fine,
+                                int64_t n_fine, int64_t out_stride, double* out_dev, int device, void* stream)
+{
+    if (!coarse_dev || !out_dev) return fail(TDSE_ERR_ARG, "tdse_resample_field: NULL buffer");
+    if (n_rows < 1 || n_rows > (int64_t(1) << 31)) return fail(TDSE_ERR_ARG, "tdse_resample_field: n_rows out of range");
+    if (M < 2 || M > 8192) return fail(TDSE_ERR_ARG, "tdse_resample_field: M out of [2, 8192]");
+    if (!is_finite(dt_coarse) || !(dt_coarse > 0.0) || !is_finite(dt_fine) || !(dt_fine > 0.0))
+        return fail(TDSE_ERR_ARG, "tdse_resample_field: steps must be finite and > 0");
+    if (n_fine < 1 || out_stride < n_fine) return fail(TDSE_ERR_ARG, "tdse_resample_field: need 1 <= n_fine <= out_stride");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(TDSE_ERR_ARG, "tdse_resample_field: no such CUDA device");
+    DeviceGuard guard(device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    void* d_coef = nullptr;
+    cudaError_t e = cudaMalloc(&d_coef, sizeof(double2) * (size_t)n_rows * (M / 2 + 1));
+    if (e == cudaSuccess) e = launch_resample_field(coarse_dev, n_rows, M, dt_coarse, dt_fine, n_fine, out_stride, out_dev,
+                                                    d_coef, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_coef);
+    if (e != cudaSuccess) return cuda_fail(e, "tdse_resample_field");
+    return TDSE_OK;
+}
+
 tdse_status tdse_spectrum(const double* a_dev, const int64_t* offsets_host, int64_t n_rows, double dt, int64_t k_begin,
                           int64_t k_end, double* S_dev, void* stream)
 {

@@ -143,6 +143,11 @@ cudaError_t launch_energy_distribution(int mixed, const GroupDesc* d_groups, con
                                        int scheme, void* d_piv, const int64_t* d_piv_off, int64_t piv_elems,
                                        void* d_scratch, int n_max, int sm_count, double* P_out, cudaStream_t st);
 
+// Field ingestion (tdse_field.cu): DFT coefficients of every coarse row (n_rows x (M/2 + 1) complex
+// doubles in d_coef), then the zero-padded interpolant at n_fine samples per row.
+cudaError_t launch_resample_field(const double* coarse, int64_t n_rows, int M, double dt_c, double dt_f,
+                                  int64_t n_fine, int64_t out_stride, double* out, void* d_coef, cudaStream_t st);
+
 // Persistent NUMEROV_SPLIT propagation (same scheduler, scratch and layouts; tables nw/nl/nc/nf).
 cudaError_t launch_propagate_numerov(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
                                      const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,

@@ -21,7 +21,7 @@ _lib = None
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
-           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_last_error")
+           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -97,6 +97,8 @@ def load(path: str | None = None):
                                 ctypes.POINTER(tdse_tune_trial), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp]
     L.tdse_set_layout.argtypes = [_vp, ctypes.c_int32]
     L.tdse_set_wait_limit.argtypes = [_vp, ctypes.c_int64]
+    L.tdse_resample_field.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int, _vp]
     L.tdse_energy_distribution.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
@@ -318,6 +320,20 @@ def spectrum(a, offsets, dt, k_begin, k_end, out=None, stream=None):
         out = torch.empty((n_rows, k_end - k_begin), dtype=torch.float64, device=a.device)
     _check(load().tdse_spectrum(_dev_ptr(a, "a"), offs.ctypes.data_as(_i64p), n_rows, float(dt), int(k_begin),
                                 int(k_end), _dev_ptr(out, "S"), _stream_ptr(stream)))
+    return out
+
+
+def resample_field(coarse, dt_coarse, dt_fine, n_fine, out=None, out_stride=None, stream=None):
+    """Zero-padded DFT interpolation of coarse field rows (see tdse_resample_field).  coarse: float64
+    CUDA tensor (n_rows, M); returns (n_rows, out_stride) with the first n_fine columns written."""
+    import torch
+    n_rows, M = coarse.shape
+    stride = int(out_stride or n_fine)
+    if out is None:
+        out = torch.zeros((n_rows, stride), dtype=torch.float64, device=coarse.device)
+    _check(load().tdse_resample_field(_dev_ptr(coarse.contiguous(), "coarse"), int(n_rows), int(M), float(dt_coarse),
+                                      float(dt_fine), int(n_fine), stride, _dev_ptr(out, "out"),
+                                      int(coarse.device.index or 0), _stream_ptr(stream)))
     return out
 
 
