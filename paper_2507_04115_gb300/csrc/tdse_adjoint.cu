@@ -271,33 +271,38 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
                 __syncthreads();
                 // C: back substitution, mu = conj(y), lambda^n = 2 mu - M lambda^{n+1} + g^n, field gradient
                 ObsSums o{0.0, 0.0, norm_term};
+                // mu = conj(y) = (Y_r, -Y_i) / beta; the 1/beta is folded into the constants below:
+                // 2 mu = tb (Y_r, -Y_i) with tb = 2/beta, and x Im(conj(mu)(psi + psi~)) sums
+                // x (Y_r s_i + Y_i s_r) with the 1/beta applied to the total.  The local gradient
+                // weight 2 dx (gd_n x_j + ga_n (dV_j + E_n)) = cx x_j + (cv dV_j + cE).
+                const double tb = 2.0 * geo.inv_beta;
+                const double cx = 2.0 * dx * gdn, cv = 2.0 * dx * gan, cE = cv * En;
+                const Fma64& F = geo.F;
                 substitute(geo, sc, [&](int j, double Yr, double Yi) {
-                    const double mur = Yr * geo.inv_beta, mui = -Yi * geo.inv_beta;
-                    const double mm = (j < jm_lo || j > jm_hi) ? __ldg(tab_m + j) : 1.0;
                     double2* lp = lam + geo.at(j);
-                    const double2 lv = *lp;
-                    const double vr = mm * lv.x, vi = mm * lv.y;
-                    double2 p0;
-                    if (pt0) {
-                        const double2 q0 = ld_cg(pt0 + geo.at(j));
-                        p0 = make_double2(mm * q0.x, mm * q0.y);
-                    } else {
-                        p0 = ld_cg(cks + geo.at(j));
+                    double2 v = *lp;   // M lambda^{n+1}
+                    double2 p0;        // psi^n = M psi~^n (the checkpoint at the interval start)
+                    if (pt0) p0 = ld_cg(pt0 + geo.at(j));
+                    else p0 = ld_cg(cks + geo.at(j));
+                    if (j < jm_lo || j > jm_hi) {
+                        const double mm = __ldg(tab_m + j);
+                        v = make_double2(F.mul(mm, v.x), F.mul(mm, v.y));
+                        if (pt0) p0 = make_double2(F.mul(mm, p0.x), F.mul(mm, p0.y));
                     }
                     const double2 p1 = ld_cg(pt1 + geo.at(j));
                     const double2 xv = __ldg(tab_xv2 + j);
-                    const double wgt = 2.0 * dx * fma(gdn, xv.x, gan * (xv.y + En));
+                    const double wgt = fma(cx, xv.x, fma(cv, xv.y, cE));
                     if (active)
-                        *lp = make_double2(fma(2.0, mur, fma(wgt, p0.x, -vr)), fma(2.0, mui, fma(wgt, p0.y, -vi)));
-                    const double sr = p0.x + p1.x, si = p0.y + p1.y;
-                    o.n = fma(xv.x, fma(mur, si, -mui * sr), o.n);
+                        *lp = make_double2(fma(tb, Yr, fma(wgt, p0.x, -v.x)), fma(-tb, Yi, fma(wgt, p0.y, -v.y)));
+                    const double sr = F.add(p0.x, p1.x), si = F.add(p0.y, p1.y);
+                    o.n = fma(xv.x, fma(Yr, si, F.mul(Yi, sr)), o.n);
                     o.x = fma(p0.x, p0.x, fma(p0.y, p0.y, o.x));
                 });
                 const ObsSums t = adj_reduce(o, geo, red, P);
                 if (w == 0 && geo.q == 0) {
                     if (term) gE[row + nt] += ga1 * dx * t.v;
                     if (active) {
-                        const double gbar = h * t.n;
+                        const double gbar = h * geo.inv_beta * t.n;
                         gE[row + n] += 0.5 * gbar + gan * dx * t.x;
                         gE[row + n + 1] += 0.5 * gbar;
                     }
