@@ -183,9 +183,11 @@ def test_chunk_with_sample_base_streaming(env):
     b.close()
 
 
-def test_volume_batch_full_size_sampled(env):
-    """The 8192 x 4096 volume batch at full size with the default plan the benchmark uses, for the
-    first 600 steps; eight sampled instances checked one by one against the oracle."""
+@pytest.mark.parametrize("launch", [(0, 0, 0, 0), (12, 1, 16, 0)])
+def test_volume_batch_full_size_sampled(env, launch):
+    """The 8192 x 4096 volume batch at full size, with the planner's default shape and with the shape
+    the benchmark's autotuner picks (12 warps per CTA, one CTA per SM, 16-step slices), for the first
+    600 steps; eight sampled instances checked one by one against the oracle."""
     tdse, oracle = env
     from paper_2507_04115_gb300 import inputs
     wl = inputs.volume_batch()
@@ -197,6 +199,8 @@ def test_volume_batch_full_size_sampled(env):
     E = torch.empty((n, steps + 1), dtype=torch.float64, device=dev)
     inputs.sin2_pulse_batch(steps, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
     b = tdse.Batch([N] * n, dx, a, [steps] * n, dt, absorber=(wl.mask_width, wl.mask_exponent))
+    if any(launch):
+        b.set_launch(*launch)
     plan = b.plan()
     assert plan["n_groups"] == n // 32 and plan["ctas"] >= 1
     b.ground_state(**GS_KW)
@@ -216,6 +220,62 @@ def test_volume_batch_full_size_sampled(env):
         assert _rel(dh[i], d_o) < RTOL_SERIES, i
         assert _rel(ah[i], a_o) < RTOL_SERIES, i
     b.close()
+
+
+def _full_size_prefix(tdse, oracle, wl, precision, steps, n_sample, tol, seed):
+    """A full-size workload batch with each instance's own Nt, laid out like the benchmark (rows of
+    steps + 1 samples), propagated over its first `steps` steps with the planner's shape;
+    n_sample instances compared one by one with the oracle."""
+    from paper_2507_04115_gb300 import inputs
+    n = wl.n_inst
+    classes = sorted(set(zip(wl.N.tolist(), wl.dx.tolist())))
+    soft = {c: oracle.fit_softening(wl.target_energy, c[0], c[1]) for c in classes}
+    a = np.array([soft[(int(N_), float(d_))] for N_, d_ in zip(wl.N, wl.dx)])
+    dev = torch.device("cuda", 0)
+    offs = np.arange(n + 1, dtype=np.int64) * (steps + 1)
+    Tp = wl.n_cycles * 2 * np.pi / wl.omega
+    t = torch.arange(steps + 1, dtype=torch.float64, device=dev)[None, :] * wl.dt
+    Tpt = torch.as_tensor(Tp, device=dev)[:, None]
+    env_ = torch.where(t <= Tpt, torch.sin(np.pi * t / Tpt) ** 2, torch.zeros_like(t))
+    E = (torch.as_tensor(wl.E0, device=dev)[:, None] * env_ *
+         torch.cos(torch.as_tensor(wl.omega, device=dev)[:, None] * (t - 0.5 * Tpt) + torch.as_tensor(wl.phi, device=dev)[:, None]))
+    Ef = E.reshape(-1).contiguous()
+    b = tdse.Batch(wl.N, wl.dx, a, wl.n_steps, wl.dt, row_offsets=offs, absorber=(wl.mask_width, wl.mask_exponent),
+                   precision=precision)
+    b.ground_state(**GS_KW)
+    d = torch.zeros_like(Ef)
+    acc = torch.zeros_like(Ef)
+    b.propagate(Ef, d, acc, 0, steps)
+    torch.cuda.synchronize()
+    assert b.check() == -1
+    b.close()
+    ah = acc.view(n, steps + 1).cpu().numpy()
+    dh = d.view(n, steps + 1).cpu().numpy()
+    Eh = E.cpu().numpy()
+    for i in inputs.subsample(n, n_sample, seed):
+        N_, dx_ = int(wl.N[i]), float(wl.dx[i])
+        psi0, _, _ = oracle.ground_state(N_, dx_, a[i], **GS_KW)
+        m = oracle.mask(N_, dx_, wl.mask_width, wl.mask_exponent)
+        _, d_o, a_o = oracle.propagate(psi0, Eh[i], dx_, wl.dt, a[i], mask_values=m)
+        assert _rel(dh[i], d_o) < tol, i
+        assert _rel(ah[i], a_o) < tol, i
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uneven_batch_full_size_prefix(env, precision):
+    """The 16384-instance uneven batch (N 1024..8192, two dx, Nt 22064..198575) at full size in one
+    persistent launch, first 300 steps; six sampled instances against the oracle."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    _full_size_prefix(tdse, oracle, inputs.uneven_batch(), precision, 300, 6, RTOL_SERIES if precision == 0 else 2e-3, 102)
+
+
+def test_large_volume_mixed_full_size_prefix(env):
+    """The 131072 x 4096 large volume in MIXED precision at full size, first 200 steps; four sampled
+    instances against the FP64 oracle at the MIXED bound."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    _full_size_prefix(tdse, oracle, inputs.large_volume(), 1, 200, 4, 2e-3, 104)
 
 
 def test_batch_position_invariance(env):
