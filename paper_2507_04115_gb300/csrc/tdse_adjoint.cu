@@ -68,20 +68,28 @@ __device__ __forceinline__ ObsSums adj_reduce(ObsSums o, const AdjGeom& g, doubl
     return reduce_obs(o, red, P);
 }
 
-// Forward elimination of A y = v over the lane's sweep rows (v from `src`, a callable giving the
-// right-hand side at point j), writing (gamma, D) rows to the scratch.
+// Forward elimination of A y = v over the lane's sweep rows (v from `rhs`, a callable giving the
+// right-hand side at point j), writing (gamma, D) rows to the scratch.  The right-hand side and the
+// table entry are loaded two rows ahead of the recurrence (they do not depend on it).
 template <class Rhs>
 __device__ __forceinline__ void eliminate(const AdjGeom& g, double Eb, const double2* __restrict__ tab_ab2,
                                           double2* __restrict__ sc, Rhs rhs)
 {
     const int lane = threadIdx.x & 31;
+    auto fetch = [&](int rr) {
+        const int j = g.base + rr;
+        return (rr < g.nrows && (unsigned)j < (unsigned)g.N) ? rhs(j) : make_double2(0.0, 0.0);
+    };
     double cr = 0.0, ci = 0.0, Dr = 0.0, Di = 0.0;
     double2* r = sc;
+    double2 va = fetch(0), vb = fetch(1);
     for (int rr = 0; rr < g.nrows; ++rr) {
+        const double2 v = va;
+        va = vb;
+        vb = fetch(rr + 2);
         const int j = g.base + rr;
         const bool in = (unsigned)j < (unsigned)g.N;
         const int jc = min(max(j, 0), g.N - 1);
-        const double2 v = in ? rhs(jc) : make_double2(0.0, 0.0);
         const double2 t = __ldg(tab_ab2 + jc);
         const Fma64& F = g.F;
         const double Qr = F.add(ci, g.inv_beta);
@@ -99,23 +107,36 @@ __device__ __forceinline__ void eliminate(const AdjGeom& g, double Eb, const dou
     }
 }
 
-// Back substitution over rows nrows-1 .. K, calling own(j, Yr, Yi) on the own segment's points.
-template <class Own>
-__device__ __forceinline__ void substitute(const AdjGeom& g, const double2* __restrict__ sc, Own own)
+// Back substitution over rows nrows-1 .. K.  On the own segment's points, fetch(j) loads what the
+// update needs (independent of Y, so it is issued one row ahead together with the next scratch
+// row) and own(j, Yr, Yi, payload) consumes it.
+template <class Fetch, class Own>
+__device__ __forceinline__ void substitute(const AdjGeom& g, const double2* __restrict__ sc, Fetch fetch, Own own)
 {
     const int lane = threadIdx.x & 31;
+    auto is_own = [&](int rr) { return rr >= g.K && rr < g.K + g.m && g.base + rr < g.N; };
+    using Payload = decltype(fetch(0));
     double Yr = 0.0, Yi = 0.0;
+    if (g.nrows <= g.K) return;
     const double2* r = sc + (int64_t)(g.nrows - 1) * (2 * kLanes);
+    double2 ga = r[lane], da = r[kLanes + lane];
+    Payload pa{};
+    if (is_own(g.nrows - 1)) pa = fetch(g.base + g.nrows - 1);
     for (int rr = g.nrows - 1; rr >= g.K; --rr) {
         const int j = g.base + rr;
-        const double2 g2 = r[lane];
-        const double2 d2 = r[kLanes + lane];
+        const double2 g2 = ga, d2 = da;
+        const Payload pl = pa;
         r -= 2 * kLanes;
+        if (rr - 1 >= g.K) {
+            ga = r[lane];
+            da = r[kLanes + lane];
+            if (is_own(rr - 1)) pa = fetch(j - 1);
+        }
         const double nr = fma(g2.x, Yr, fma(-g2.y, Yi, d2.x));
         const double ni = fma(g2.x, Yi, fma(g2.y, Yr, d2.y));
         Yr = j < g.N ? nr : 0.0;
         Yi = j < g.N ? ni : 0.0;
-        if (rr < g.K + g.m && j < g.N) own(j, Yr, Yi);
+        if (is_own(rr)) own(j, Yr, Yi, pl);
     }
 }
 
@@ -128,9 +149,8 @@ __device__ __forceinline__ void fwd_step(double2* __restrict__ ps, const AdjGeom
 {
     eliminate(g, Eb, tab_ab2, sc, [&](int j) { return ld_cg(ps + g.at(j)); });
     __syncthreads();
-    substitute(g, sc, [&](int j, double Yr, double Yi) {
+    substitute(g, sc, [&](int j) { return ld_cg(ps + g.at(j)); }, [&](int j, double Yr, double Yi, const double2& old) {
         double2* pp = ps + g.at(j);
-        const double2 old = *pp;
         double xr = fma(g.two_over_beta, Yr, -old.x);
         double xi = fma(g.two_over_beta, Yi, -old.y);
         if (tape) tape[g.at(j)] = active ? make_double2(xr, xi) : old;
@@ -278,19 +298,28 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
                 const double tb = 2.0 * geo.inv_beta;
                 const double cx = 2.0 * dx * gdn, cv = 2.0 * dx * gan, cE = cv * En;
                 const Fma64& F = geo.F;
-                substitute(geo, sc, [&](int j, double Yr, double Yi) {
+                struct Row {
+                    double2 v, p0, p1, xv;
+                };
+                auto fetch = [&](int j) {
+                    Row q;
+                    q.v = ld_cg(lam + geo.at(j));                                  // lambda^{n+1}
+                    q.p0 = pt0 ? ld_cg(pt0 + geo.at(j)) : ld_cg(cks + geo.at(j));  // psi~^n or psi^n
+                    q.p1 = ld_cg(pt1 + geo.at(j));                                 // psi~^{n+1}
+                    q.xv = __ldg(tab_xv2 + j);
+                    return q;
+                };
+                substitute(geo, sc, fetch, [&](int j, double Yr, double Yi, const Row& q) {
                     double2* lp = lam + geo.at(j);
-                    double2 v = *lp;   // M lambda^{n+1}
-                    double2 p0;        // psi^n = M psi~^n (the checkpoint at the interval start)
-                    if (pt0) p0 = ld_cg(pt0 + geo.at(j));
-                    else p0 = ld_cg(cks + geo.at(j));
+                    double2 v = q.v;     // M lambda^{n+1}
+                    double2 p0 = q.p0;   // psi^n = M psi~^n (the checkpoint at the interval start)
                     if (j < jm_lo || j > jm_hi) {
                         const double mm = __ldg(tab_m + j);
                         v = make_double2(F.mul(mm, v.x), F.mul(mm, v.y));
                         if (pt0) p0 = make_double2(F.mul(mm, p0.x), F.mul(mm, p0.y));
                     }
-                    const double2 p1 = ld_cg(pt1 + geo.at(j));
-                    const double2 xv = __ldg(tab_xv2 + j);
+                    const double2 p1 = q.p1;
+                    const double2 xv = q.xv;
                     const double wgt = fma(cx, xv.x, fma(cv, xv.y, cE));
                     if (active)
                         *lp = make_double2(fma(tb, Yr, fma(wgt, p0.x, -v.x)), fma(-tb, Yi, fma(wgt, p0.y, -v.y)));
