@@ -117,6 +117,8 @@ __global__ void k_ed_solve(const GroupDesc* __restrict__ groups, const ClassDesc
         // forward: d'_j = (r_j - a_j d'_{j-1}) / w_j
         double dr = 0.0, di = 0.0;
         Cx pm = Cx{0, 0}, pc = ps[0], pn = N > 1 ? ps[I] : Cx{0, 0};
+        // 1/w rows and (below) the scratch and c' rows are loaded two rows ahead of the recurrence
+        double2 wa = W[0], wb = N > 1 ? W[nE_pad] : make_double2(0.0, 0.0);
         for (int j = 0; j < N; ++j) {
             double rr, ri;
             if (scheme == 0) {
@@ -137,7 +139,9 @@ __global__ void k_ed_solve(const GroupDesc* __restrict__ groups, const ClassDesc
             // u = r - a d'
             const double ur = fma(-a.x, dr, fma(a.y, di, rr));
             const double ui = fma(-a.x, di, fma(-a.y, dr, ri));
-            const double2 iw = W[(int64_t)j * nE_pad];
+            const double2 iw = wa;
+            wa = wb;
+            if (j + 2 < N) wb = W[(int64_t)(j + 2) * nE_pad];
             dr = fma(ur, iw.x, F.mul(-ui, iw.y));
             di = fma(ur, iw.y, F.mul(ui, iw.x));
             sc[(int64_t)j * kLanes + lane] = make_double2(dr, di);
@@ -147,9 +151,20 @@ __global__ void k_ed_solve(const GroupDesc* __restrict__ groups, const ClassDesc
         }
         // backward: y_j = d'_j - c'_j y_{j+1}, sum |y|^2
         double yr = 0.0, yi = 0.0, s = 0.0;
+        double2 da = sc[(int64_t)(N - 1) * kLanes + lane], ca = Cp[(int64_t)(N - 1) * nE_pad];
+        double2 db = make_double2(0.0, 0.0), cb = db;
+        if (N > 1) {
+            db = sc[(int64_t)(N - 2) * kLanes + lane];
+            cb = Cp[(int64_t)(N - 2) * nE_pad];
+        }
         for (int j = N - 1; j >= 0; --j) {
-            const double2 d2 = sc[(int64_t)j * kLanes + lane];
-            const double2 cp = Cp[(int64_t)j * nE_pad];
+            const double2 d2 = da, cp = ca;
+            da = db;
+            ca = cb;
+            if (j - 2 >= 0) {
+                db = sc[(int64_t)(j - 2) * kLanes + lane];
+                cb = Cp[(int64_t)(j - 2) * nE_pad];
+            }
             const double nr = fma(-cp.x, yr, fma(cp.y, yi, d2.x));
             yi = fma(-cp.x, yi, fma(-cp.y, yr, d2.y));
             yr = nr;
