@@ -667,7 +667,7 @@ def other_workload(args):
         _line("field ingestion samples/s (Sec. 4.2, zero-padded DFT interpolation)", float(n) * n_fine / t,
               "fine samples/s", args, "%d rows x %d coarse samples (dt %g) -> %d samples (dt %g)" % (n, M, dt_c, n_fine, dt_f),
               dict(rows=n, M=M, dt_coarse=dt_c, dt_fine=dt_f, n_fine=n_fine), dtype="f64",
-              flops_per_sample=6 * (M // 2 + 1), seconds_per_call=t)
+              fp64_instructions_per_sample=6 * (M // 2 + 1), seconds_per_call=t)
         return
 
     if args.workload == "resolvent":

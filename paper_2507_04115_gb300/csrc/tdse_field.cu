@@ -83,13 +83,14 @@ cudaError_t launch_resample_field(const double* coarse, int64_t n_rows, int M, d
 {
     if (n_rows == 0 || n_fine == 0) return cudaSuccess;
     const int K = M / 2;
-    static bool attr_set = false;   // rows up to 8192 samples: 64 KB of shared memory per CTA
-    if (!attr_set) {
+    static std::atomic<bool> attr_set[kMaxAttrDevices];   // rows up to 8192 samples: 64 KB of shared memory per CTA
+    int dev = 0;
+    if (attr_needed(attr_set, &dev)) {
         cudaError_t e = cudaFuncSetAttribute(k_field_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_field_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, 4097 * 16);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_done(attr_set, dev);
     }
     double2* coef = static_cast<double2*>(d_coef);
     for (int64_t r0 = 0; r0 < n_rows; r0 += 65535) {

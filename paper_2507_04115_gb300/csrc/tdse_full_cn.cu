@@ -535,12 +535,13 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
     if (mixed && (ring < kMinRing || ring > kMaxRing)) return cudaErrorInvalidValue;
     const size_t smem = full_cn_smem_bytes(mixed, P, ring);
     if (mixed) {
-        static bool attr_set = false;
-        if (!attr_set) {
+        static std::atomic<bool> attr_set[kMaxAttrDevices];
+        int dev = 0;
+        if (attr_needed(attr_set, &dev)) {
             e = cudaFuncSetAttribute(k_propagate_full_cn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)full_cn_smem_max_bytes());
             if (e != cudaSuccess) return e;
-            attr_set = true;
+            attr_done(attr_set, dev);
         }
         k_propagate_full_cn<true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -79,6 +80,20 @@ inline int class_segments(int N, int K, int warps)
     if (K == 0) return 1;
     const int max_P = std::max(1, N / std::max(4 * K, 16));
     return std::max(1, std::min(warps, max_P));
+}
+
+// Function attributes (the dynamic shared memory limit) belong to a device: a launcher that raises
+// one keeps a flag per device ordinal and sets it on the first launch on each device.
+constexpr int kMaxAttrDevices = 64;
+inline bool attr_needed(const std::atomic<bool>* flags, int* dev)
+{
+    *dev = 0;
+    cudaGetDevice(dev);
+    return *dev < 0 || *dev >= kMaxAttrDevices || !flags[*dev].load(std::memory_order_acquire);
+}
+inline void attr_done(std::atomic<bool>* flags, int dev)
+{
+    if (dev >= 0 && dev < kMaxAttrDevices) flags[dev].store(true, std::memory_order_release);
 }
 
 // Segment length of a group: P_g warps x L lanes per instance share the N points.
