@@ -227,8 +227,8 @@ tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);
  * into L times more segments: more halo work per point, but 32/L-instance groups occupy L times
  * more SMs, which pays when the batch is too small to fill the GPU.  L = 0 (the default at
  * creation) picks L from a cost model of the batch: FP64 warp instructions of a step per group
- * against the number of SMs.  NUMEROV_SPLIT batches and classes whose halo cannot be truncated
- * (dt/(4 dx^2) >= 0.85) always use L = 1.  The wavefunction state is discarded (call before
+ * against the number of SMs.  Classes whose sweeps cannot be truncated (decay rate per point
+ * dt/(4 dx^2) for FULL_CN, the largest Numerov factor for NUMEROV_SPLIT, >= 0.85) always use L = 1.  The wavefunction state is discarded (call before
  * tdse_ground_state, tdse_set_psi or tdse_copy_state); synchronises the device and reallocates.
  * Returns TDSE_ERR_ARG for L outside {0, 1, 2, 4, 8, 16, 32}. */
 tdse_status tdse_set_layout(tdse_batch* batch, int32_t lanes_per_instance);

@@ -241,11 +241,16 @@ int default_warps(const tdse_batch* b)
 // 2K forward rows and K back-substitution rows), with m = N / (P L).  The step time is the larger
 // of (total work / SMs) and the longest single group (one group runs on one SM).  L = 1 keeps
 // 32 instances per warp; a larger L is taken only when it is clearly faster, i.e. when the
-// batch has too few groups to occupy the SMs.  NUMEROV_SPLIT and classes without a usable halo
-// keep L = 1.
+// batch has too few groups to occupy the SMs.  Classes without a usable halo keep L = 1.
+// Decay rate per point of a class's truncated sweeps: |gamma| <= beta for FULL_CN, max(|L|, |C|)
+// of the factors for NUMEROV_SPLIT.
+double class_decay(const tdse_batch* b, const ClassDesc& C)
+{
+    return b->scheme == TDSE_NUMEROV_SPLIT ? C.rho : C.beta;
+}
+
 int model_lanes(const tdse_batch* b, const std::vector<int64_t>& class_count)
 {
-    if (b->scheme == TDSE_NUMEROV_SPLIT) return 1;
     const int warps = b->warps_override > 0 ? b->warps_override : default_warps(b);
     double best_t = 0.0;
     int best_L = 1;
@@ -253,7 +258,7 @@ int model_lanes(const tdse_batch* b, const std::vector<int64_t>& class_count)
         double work = 0.0, longest = 0.0;
         for (size_t c = 0; c < b->classes.size(); ++c) {
             const ClassDesc& C = b->classes[c];
-            const int K = halo_for_beta(C.beta);
+            const int K = halo_for_beta(class_decay(b, C));
             const int Lc = K == 0 ? 1 : L;
             const int P = Lc == 1 ? class_segments(C.N, K, warps) : std::max(1, std::min(warps, C.N / Lc));
             const int m = group_segment_length(C.N, P, Lc);
@@ -279,10 +284,9 @@ tdse_status build_groups(tdse_batch* b)
     const int64_t n_inst = b->n_inst;
     std::vector<int64_t> class_count(n_cls, 0);
     for (int64_t i = 0; i < n_inst; ++i) ++class_count[b->inst_class[i]];
-    const int L = b->lanes_request > 0 ? (b->scheme == TDSE_NUMEROV_SPLIT ? 1 : b->lanes_request)
-                                       : model_lanes(b, class_count);
+    const int L = b->lanes_request > 0 ? b->lanes_request : model_lanes(b, class_count);
     b->class_L.assign(n_cls, 1);
-    for (int c = 0; c < n_cls; ++c) b->class_L[c] = halo_for_beta(b->classes[c].beta) == 0 ? 1 : L;
+    for (int c = 0; c < n_cls; ++c) b->class_L[c] = halo_for_beta(class_decay(b, b->classes[c])) == 0 ? 1 : L;
 
     std::vector<int64_t> order(n_inst);
     for (int64_t i = 0; i < n_inst; ++i) order[i] = i;
@@ -385,7 +389,7 @@ tdse_status build_plan(tdse_batch* b)
     b->class_K.assign(n_cls, 0);
     for (int c = 0; c < n_cls; ++c) {
         const ClassDesc& C = b->classes[c];
-        int K = halo_for_beta(b->scheme == TDSE_NUMEROV_SPLIT ? C.rho : C.beta);
+        int K = halo_for_beta(class_decay(b, C));
         const int L = b->class_L[c];
         // lane-split classes use every warp (short segments are the price of filling the GPU)
         const int P = L == 1 ? class_segments(C.N, K, b->warps) : std::max(1, std::min(b->warps, C.N / L));
@@ -538,7 +542,6 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     if ((e = dev_alloc(&b->d_tab, (size_t)tab_total)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(tables)"));
     if ((e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
-    if ((st = build_groups(b)) != TDSE_OK) return bail(st);
     int64_t gs_total = 0;
     std::vector<int64_t> gs_off(n_cls);
     for (int c = 0; c < n_cls; ++c) {
@@ -569,6 +572,9 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
         if ((e = cudaMemcpy(b->d_cls, b->classes.data(), sizeof(ClassDesc) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(cuda_fail(e, "cudaMemcpy(classes)"));
     }
+    // the grouping (lanes per instance) needs each class's halo, which for NUMEROV_SPLIT comes from
+    // the factors just computed
+    if ((st = build_groups(b)) != TDSE_OK) return bail(st);
     if ((st = build_plan(b)) != TDSE_OK) return bail(st);
     *out = b;
     return TDSE_OK;

@@ -16,6 +16,176 @@ namespace tdse {
 // point, and K is chosen from that bound.  Then psi^{n+1} = m exp(-i dt E_n x) (2y - psi).
 // The phase exp(-i dt E_n x_j) runs as a complex rotation from the segment end, re-seeded from
 // sincos every 64 points (double) or 8 points (float).
+// One scheduling slice of a lane-split group (G.I = 32/L instances, each over L lanes of every
+// warp): the same lane geometry as the FULL_CN kernel's lane-split path -- lane l of warp w holds
+// instance l % I and sweeps segment sigma = w L + l / I over rows r = 0 .. m + 2K - 1 at points
+// sigma m - K + r, rows before the first wall restart the forward recurrence at zero and rows at or
+// beyond the far wall restart the back substitution, so all lanes run the same trip counts.  The
+// own segment is rows K .. K + m - 1; the phase rotation is re-seeded at its first point.
+// Observables are summed over the L lanes by shuffles, then over the warps, in double.
+template <bool kMixed>
+__device__ __forceinline__ void numerov_split_slice(
+    const GroupDesc& G, const ClassDesc& C, const Fma64& F, typename Prec<kMixed>::C* __restrict__ ps,
+    const double2* __restrict__ tW, const double2* __restrict__ tL, const double2* __restrict__ tC,
+    const float2* __restrict__ tF, const double2* __restrict__ tab_xv2, const double* __restrict__ tab_m, int jm_lo,
+    int jm_hi, int64_t nt, int64_t row, int64_t slot, int64_t n0, int64_t n1, bool initial, double dt,
+    const double* __restrict__ E, double* __restrict__ d_out, double* __restrict__ a_out, int64_t sample_base,
+    typename Prec<kMixed>::C* __restrict__ sc, double* red, int* status)
+{
+    using R = typename Prec<kMixed>::R;
+    using Cx = typename Prec<kMixed>::C;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int P = blockDim.x >> 5;
+    const int I = G.I, L = kLanes / G.I;
+    const int i = lane & (I - 1), q = lane / I;
+    const int N = G.N, K = G.K, m = G.m;
+    const int sigma = w * L + q;
+    const int nrows = w < G.P ? m + 2 * K : 0;   // warp-uniform
+    const int base = sigma * m - K;
+    const int s_own = min(N, sigma * m), e_own = min(N, sigma * m + m);
+    const double dx = C.dx;
+    const double x0 = -0.5 * (N - 1) * dx;
+    auto lane_sum = [&](ObsSums o) {
+        for (int off = I; off < kLanes; off <<= 1) {
+            o.n += __shfl_xor_sync(0xffffffffu, o.n, off);
+            o.x += __shfl_xor_sync(0xffffffffu, o.x, off);
+            o.v += __shfl_xor_sync(0xffffffffu, o.v, off);
+        }
+        return o;
+    };
+    auto at = [&](int j) { return ps + (int64_t)j * I + i; };
+
+    if (initial) {
+        ObsSums o{0.0, 0.0, 0.0};
+        if (w < G.P)
+            for (int j = s_own; j < e_own; ++j) {
+                const Cx p = ld_cg(at(j));
+                const double rho = fma((double)p.x, (double)p.x, (double)p.y * (double)p.y);
+                const double2 xv = __ldg(tab_xv2 + j);
+                o.n += rho;
+                o.x = fma(xv.x, rho, o.x);
+                o.v = fma(xv.y, rho, o.v);
+            }
+        const ObsSums t = reduce_obs(lane_sum(o), red, P);
+        if (w == 0 && q == 0 && nt >= 0) {
+            const double E0 = E[row - sample_base];
+            d_out[row - sample_base] = t.x * dx;
+            a_out[row - sample_base] = fma(E0, t.n, t.v) * dx;
+        }
+        __syncthreads();
+    }
+
+    for (int64_t n = n0; n < n1; ++n) {
+        const bool active = n < nt;
+        double En = 0.0, En1 = 0.0;
+        if (active) {
+            En = E[row + n - sample_base];
+            En1 = E[row + n + 1 - sample_base];
+        }
+
+        // forward: d_j = W_j (psi_{j-1} + 10 psi_j + psi_{j+1}) - L_j d_{j-1}
+        {
+            auto load = [&](int j) -> Cx { return (unsigned)j < (unsigned)N ? ld_cg(at(j)) : mk(R(0), R(0)); };
+            Cx pm = nrows > 0 ? load(base - 1) : mk(R(0), R(0));
+            Cx pc = nrows > 0 ? load(base) : mk(R(0), R(0));
+            Cx pn = nrows > 0 ? load(base + 1) : mk(R(0), R(0));
+            R dr = 0, di = 0;
+            Cx* r = sc;
+            for (int rr = 0; rr < nrows; ++rr) {
+                const int j = base + rr;
+                const Cx nx = rr + 1 < nrows ? load(j + 2) : mk(R(0), R(0));
+                const bool in = (unsigned)j < (unsigned)N;
+                const int jc = min(max(j, 0), N - 1);
+                const R rre = fma(R(10), pc.x, F.add(pm.x, pn.x));
+                const R rim = fma(R(10), pc.y, F.add(pm.y, pn.y));
+                R wr, wi, lr, li;
+                if constexpr (kMixed) {
+                    const float2 fw = __ldg(tF + 3 * jc), fl = __ldg(tF + 3 * jc + 1);
+                    wr = fw.x; wi = fw.y; lr = fl.x; li = fl.y;
+                } else {
+                    const double2 tw = __ldg(tW + jc), tl = __ldg(tL + jc);
+                    wr = tw.x; wi = tw.y; lr = tl.x; li = tl.y;
+                }
+                const R nr = fma(wr, rre, fma(-wi, rim, fma(-lr, dr, F.mul(li, di))));
+                const R ni = fma(wr, rim, fma(wi, rre, fma(-lr, di, F.mul(-li, dr))));
+                dr = in ? nr : R(0);
+                di = in ? ni : R(0);
+                r[lane] = mk(dr, di);
+                r += 2 * kLanes;
+                pm = pc;
+                pc = pn;
+                pn = nx;
+            }
+        }
+        __syncthreads();   // every read of psi^n precedes any write of psi^{n+1}
+
+        // backward: y_j = d_j - C_j y_{j+1}; psi^{n+1}_j = m_j phase_j (2 y_j - psi^n_j) on the own rows
+        ObsSums o{0.0, 0.0, 0.0};
+        {
+            R wr_, wi_;
+            if constexpr (kMixed) sincosf(d2f(dt * En * dx), &wi_, &wr_);
+            else sincos(dt * En * dx, &wi_, &wr_);
+            R phr = 1, phi = 0;
+            const int reseed = kMixed ? 8 : 64;
+            int own_count = 0;
+            R yr = 0, yi = 0;
+            const Cx* r = sc + (int64_t)(nrows - 1) * (2 * kLanes);
+            for (int rr = nrows - 1; rr >= K; --rr) {
+                const int j = base + rr;
+                const Cx d2 = r[lane];
+                r -= 2 * kLanes;
+                const int jc = min(max(j, 0), N - 1);
+                R cr_, ci_;
+                if constexpr (kMixed) {
+                    const float2 fc = __ldg(tF + 3 * jc + 2);
+                    cr_ = fc.x; ci_ = fc.y;
+                } else {
+                    const double2 tc = __ldg(tC + jc);
+                    cr_ = tc.x; ci_ = tc.y;
+                }
+                const R nr = fma(-cr_, yr, fma(ci_, yi, d2.x));
+                const R ni = fma(-cr_, yi, fma(-ci_, yr, d2.y));
+                yr = j < N ? nr : R(0);   // Dirichlet restart at the far wall
+                yi = j < N ? ni : R(0);
+                if (rr < K + m && j < N) {
+                    if (own_count++ % reseed == 0) {
+                        if constexpr (kMixed) sincosf(d2f(-dt * En * (x0 + j * dx)), &phi, &phr);
+                        else sincos(-dt * En * (x0 + j * dx), &phi, &phr);
+                    }
+                    Cx* pw = at(j);
+                    const Cx old = ld_cg(pw);
+                    const R tr = fma(R(2), yr, -old.x);
+                    const R ti = fma(R(2), yi, -old.y);
+                    R xr = fma(tr, phr, F.mul(-ti, phi));
+                    R xi = fma(tr, phi, F.mul(ti, phr));
+                    const R qr = fma(phr, wr_, F.mul(-phi, wi_));   // next point: x smaller by dx
+                    phi = fma(phr, wi_, F.mul(phi, wr_));
+                    phr = qr;
+                    if (j < jm_lo || j > jm_hi) {
+                        const R mm = (R)__ldg(tab_m + j);
+                        xr = F.mul(xr, mm);
+                        xi = F.mul(xi, mm);
+                    }
+                    if (active) *pw = mk(xr, xi);
+                    const double rho = fma((double)xr, (double)xr, F.mul((double)xi, (double)xi));
+                    const double2 xv = __ldg(tab_xv2 + j);
+                    o.n = F.add(rho, o.n);
+                    o.x = fma(xv.x, rho, o.x);
+                    o.v = fma(xv.y, rho, o.v);
+                }
+            }
+        }
+        const ObsSums t = reduce_obs(lane_sum(o), red, P);   // its barrier orders this step's writes
+        if (w == 0 && q == 0 && active) {
+            const int64_t kk = row + n + 1 - sample_base;
+            d_out[kk] = t.x * dx;
+            a_out[kk] = fma(En1, t.n, t.v) * dx;
+            if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
+        }
+    }
+}
+
 template <bool kMixed>
 __global__ void __launch_bounds__(512, 1)
 k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, const ClassDesc* __restrict__ cls,
@@ -56,7 +226,7 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const ClassDesc C = cls[G.cls];
         const Fma64 F{C.one, C.nzero};
         const int N = G.N, Pg = G.P, K = G.K, m = G.m;
-        const int64_t slot = G.slot0 + lane;
+        const int64_t slot = G.slot0 + (lane & (G.I - 1));   // this lane's instance
         const int64_t nt = slot_nt[slot];
         const int64_t row = slot_row[slot];
         const double dx = C.dx;
@@ -79,6 +249,11 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const int64_t n1 = min(n_end, n0 + slice);
         const double x0 = -0.5 * (N - 1) * dx;
 
+        if (G.I != kLanes) {
+            numerov_split_slice<kMixed>(G, C, F, ps, tW, tL, tC, tF, tab_xv2, tab_m, jm_lo, jm_hi, nt, row, slot, n0,
+                                        n1, kslice == 0 && step_begin == 0, dt, E, d_out, a_out, sample_base, sc, red,
+                                        status);
+        } else {
         if (kslice == 0 && step_begin == 0) {
             ObsSums o{0.0, 0.0, 0.0};
             for (int j = s; j < e; ++j) {
@@ -259,6 +434,7 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
             }
         }
+        }   // 32-wide group
 
         __threadfence();
         __syncthreads();

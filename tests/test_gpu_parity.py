@@ -448,7 +448,7 @@ def test_mixed_ragged_batch_segments(env, lanes):
 
 # ------------------------------------------------------------------------------- the paper's scheme
 
-def _numerov_case(tdse, oracle, precision, launch=None):
+def _numerov_case(tdse, oracle, precision, launch=None, lanes=1):
     from paper_2507_04115_gb300 import inputs
     rng = np.random.default_rng(21)
     n = 37
@@ -460,7 +460,8 @@ def _numerov_case(tdse, oracle, precision, launch=None):
     dev = torch.device("cuda", 0)
     Et = _device_rows(rows, offs, dev)
     b = tdse.Batch([N] * n, dx, a, nt, dt, row_offsets=offs, absorber=(20.0, 0.125), precision=precision,
-                   scheme=tdse.TDSE_NUMEROV_SPLIT)
+                   scheme=tdse.TDSE_NUMEROV_SPLIT, lanes_per_instance=lanes)
+    assert b.plan()["lanes_per_instance"] == lanes
     if launch:
         b.set_launch(*launch)
     e, _ = b.ground_state(**GS_KW)
@@ -483,17 +484,19 @@ def _numerov_case(tdse, oracle, precision, launch=None):
     return max(errs)
 
 
-def test_numerov_split_fp64_matches_oracle(env):
+@pytest.mark.parametrize("lanes", [1, 8])
+def test_numerov_split_fp64_matches_oracle(env, lanes):
     """The paper's three-substep Numerov scheme (Sec. 4.2), FP64, ragged lengths, two chunks, groups
-    moving between CTAs."""
+    moving between CTAs; 32-wide and lane-split groups."""
     tdse, oracle = env
-    assert _numerov_case(tdse, oracle, tdse.TDSE_FP64) < RTOL_SERIES
-    assert _numerov_case(tdse, oracle, tdse.TDSE_FP64, launch=(3, 1, 11, 1)) < RTOL_SERIES
+    assert _numerov_case(tdse, oracle, tdse.TDSE_FP64, lanes=lanes) < RTOL_SERIES
+    assert _numerov_case(tdse, oracle, tdse.TDSE_FP64, launch=(3, 1, 11, 1 if lanes == 1 else 2), lanes=lanes) < RTOL_SERIES
 
 
-def test_numerov_split_mixed_matches_oracle(env):
+@pytest.mark.parametrize("lanes", [1, 8])
+def test_numerov_split_mixed_matches_oracle(env, lanes):
     tdse, oracle = env
-    assert _numerov_case(tdse, oracle, tdse.TDSE_MIXED) < MIXED_SERIES
+    assert _numerov_case(tdse, oracle, tdse.TDSE_MIXED, lanes=lanes) < MIXED_SERIES
 
 
 # ------------------------------------------------------------------------------- adjoint
@@ -656,9 +659,12 @@ def test_layout_cost_model_and_psi_access(env):
     one = tdse.Batch([2000], 0.2, 1.19, [10], 0.05)
     assert one.plan()["lanes_per_instance"] == 32
     one.close()
-    # Numerov keeps 32-wide groups whatever is requested
+    # NUMEROV_SPLIT takes the requested layout too, and the model splits a single Numerov instance
     nb = tdse.Batch([512] * 3, 0.2, 1.19, [10] * 3, 0.05, scheme=tdse.TDSE_NUMEROV_SPLIT, lanes_per_instance=8)
-    assert nb.plan()["lanes_per_instance"] == 1
+    assert nb.plan()["lanes_per_instance"] == 8
+    nb.close()
+    nb = tdse.Batch([2000], 0.2, 1.19, [10], 0.05, scheme=tdse.TDSE_NUMEROV_SPLIT)
+    assert nb.plan()["lanes_per_instance"] > 1
     nb.close()
     rng = np.random.default_rng(3)
     for lanes in (1, 8, 32):
