@@ -242,6 +242,13 @@ tdse_status tdse_set_layout(tdse_batch* batch, int32_t lanes_per_instance);
 tdse_status tdse_set_launch(tdse_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
                             int32_t max_ctas);
 
+/* The layout (lanes per instance) that the cost model of tdse_set_layout would pick for a batch of
+ * these instances on a GPU with sm_count SMs, computed on the host without a GPU and without
+ * creating anything: the planning step of tdse_batch_create on its own, for capacity planning and
+ * tests.  The paper has no counterpart.  Arguments as tdse_batch_create; *lanes_out receives L. */
+tdse_status tdse_model_layout(const tdse_instance* inst_host, int64_t n_inst, double dt, tdse_precision precision,
+                              tdse_scheme scheme, int32_t sm_count, int32_t* lanes_out);
+
 /* Bound on the MIXED kernels' waits for their bulk copies (global -> shared memory), in mbarrier
  * polls; default 2^22 (a copy lands within microseconds).  A wait that runs out drains the copies
  * still in flight (with the default bound), stops using bulk copies for the rest of the launch and

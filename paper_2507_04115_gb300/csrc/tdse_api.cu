@@ -227,6 +227,39 @@ double numerov_factors(const ClassDesc& C, double dt, std::vector<double>& nw, s
     return rho;
 }
 
+// Classes: distinct (N, dx, a, Z), compared bit for bit; fills b->classes and b->inst_class.
+void build_classes(tdse_batch* b, const tdse_instance* inst_host, int64_t n_inst, double dt)
+{
+    std::map<std::tuple<int32_t, uint64_t, uint64_t, uint64_t>, int> cmap;
+    b->inst_class.resize(n_inst);
+    for (int64_t i = 0; i < n_inst; ++i) {
+        const tdse_instance& I = inst_host[i];
+        uint64_t kdx, ka, kz;
+        std::memcpy(&kdx, &I.dx, 8);
+        std::memcpy(&ka, &I.softening, 8);
+        std::memcpy(&kz, &I.charge, 8);
+        auto key = std::make_tuple(I.N, kdx, ka, kz);
+        auto it = cmap.find(key);
+        int c;
+        if (it == cmap.end()) {
+            c = (int)b->classes.size();
+            cmap.emplace(key, c);
+            ClassDesc C{};
+            C.N = I.N;
+            C.dx = I.dx;
+            C.a = I.softening;
+            C.Z = I.charge;
+            C.beta = dt / (4.0 * I.dx * I.dx);
+            C.one = 1.0;
+            C.nzero = -0.0;
+            b->classes.push_back(C);
+        } else {
+            c = it->second;
+        }
+        b->inst_class[i] = c;
+    }
+}
+
 int default_warps(const tdse_batch* b)
 {
     // measured on the 8192 x 4096 volume batch: FP64 is FP64-pipe bound with two warps per
@@ -477,35 +510,7 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     b->n_steps.assign(n_steps_host, n_steps_host + n_inst);
     b->row_off.assign(row_offsets_host, row_offsets_host + n_inst + 1);
 
-    // classes: distinct (N, dx, a, Z), compared bit for bit
-    std::map<std::tuple<int32_t, uint64_t, uint64_t, uint64_t>, int> cmap;
-    b->inst_class.resize(n_inst);
-    for (int64_t i = 0; i < n_inst; ++i) {
-        const tdse_instance& I = inst_host[i];
-        uint64_t kdx, ka, kz;
-        std::memcpy(&kdx, &I.dx, 8);
-        std::memcpy(&ka, &I.softening, 8);
-        std::memcpy(&kz, &I.charge, 8);
-        auto key = std::make_tuple(I.N, kdx, ka, kz);
-        auto it = cmap.find(key);
-        int c;
-        if (it == cmap.end()) {
-            c = (int)b->classes.size();
-            cmap.emplace(key, c);
-            ClassDesc C{};
-            C.N = I.N;
-            C.dx = I.dx;
-            C.a = I.softening;
-            C.Z = I.charge;
-            C.beta = dt / (4.0 * I.dx * I.dx);
-            C.one = 1.0;
-            C.nzero = -0.0;
-            b->classes.push_back(C);
-        } else {
-            c = it->second;
-        }
-        b->inst_class[i] = c;
-    }
+    build_classes(b, inst_host, n_inst, dt);
     const int n_cls = (int)b->classes.size();
     // mask plateau [jm_lo, jm_hi] and table offsets
     int64_t tab_total = 0;
@@ -601,6 +606,39 @@ tdse_status tdse_plan(const tdse_batch* b, tdse_plan_info* info)
     info->scratch_bytes = b->scratch_elems * (int64_t)b->cx_bytes();
     info->psi_bytes = b->psi_elems * (int64_t)b->cx_bytes();
     info->lanes_per_instance = b->class_L.empty() ? 1 : *std::max_element(b->class_L.begin(), b->class_L.end());
+    return TDSE_OK;
+}
+
+tdse_status tdse_model_layout(const tdse_instance* inst_host, int64_t n_inst, double dt, tdse_precision precision,
+                              tdse_scheme scheme, int32_t sm_count, int32_t* lanes_out)
+{
+    if (!inst_host || !lanes_out) return fail(TDSE_ERR_ARG, "tdse_model_layout: NULL argument");
+    if (n_inst < 1 || n_inst > (int64_t(1) << 31)) return fail(TDSE_ERR_ARG, "tdse_model_layout: n_inst out of range");
+    if (!is_finite(dt) || dt == 0.0) return fail(TDSE_ERR_ARG, "tdse_model_layout: dt must be finite and non-zero");
+    if (precision != TDSE_FP64 && precision != TDSE_MIXED) return fail(TDSE_ERR_ARG, "tdse_model_layout: unknown precision");
+    if (scheme != TDSE_FULL_CN && scheme != TDSE_NUMEROV_SPLIT) return fail(TDSE_ERR_ARG, "tdse_model_layout: unknown scheme");
+    if (sm_count < 1 || sm_count > 4096) return fail(TDSE_ERR_ARG, "tdse_model_layout: sm_count out of [1, 4096]");
+    for (int64_t i = 0; i < n_inst; ++i) {
+        const tdse_instance& I = inst_host[i];
+        if (I.N < 16 || I.N > (1 << 20) || !is_finite(I.dx) || I.dx <= 0.0 || !is_finite(I.softening) ||
+            I.softening <= 0.0 || !is_finite(I.charge))
+            return fail(TDSE_ERR_ARG, "tdse_model_layout: bad instance " + std::to_string(i));
+    }
+    tdse_batch tmp;   // host fields only: no device state is created
+    tmp.n_inst = n_inst;
+    tmp.dt = dt;
+    tmp.precision = precision;
+    tmp.scheme = scheme;
+    tmp.sm_count = sm_count;
+    build_classes(&tmp, inst_host, n_inst, dt);
+    if (scheme == TDSE_NUMEROV_SPLIT) {
+        std::vector<double> nw, nl, nc;
+        std::vector<float> nf;
+        for (auto& C : tmp.classes) C.rho = numerov_factors(C, dt, nw, nl, nc, nf);
+    }
+    std::vector<int64_t> count(tmp.classes.size(), 0);
+    for (int64_t i = 0; i < n_inst; ++i) ++count[tmp.inst_class[i]];
+    *lanes_out = model_lanes(&tmp, count);
     return TDSE_OK;
 }
 

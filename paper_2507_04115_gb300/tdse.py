@@ -21,7 +21,8 @@ _lib = None
 #: C-ABI entry points declared in include/tdse.h
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
-           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_last_error")
+           "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_model_layout",
+           "tdse_last_error")
 
 
 class tdse_instance(ctypes.Structure):
@@ -97,6 +98,8 @@ def load(path: str | None = None):
                                 ctypes.POINTER(tdse_tune_trial), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp]
     L.tdse_set_layout.argtypes = [_vp, ctypes.c_int32]
     L.tdse_set_wait_limit.argtypes = [_vp, ctypes.c_int64]
+    L.tdse_model_layout.argtypes = [ctypes.POINTER(tdse_instance), ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     L.tdse_resample_field.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int, _vp]
     L.tdse_energy_distribution.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp]
@@ -321,6 +324,19 @@ def spectrum(a, offsets, dt, k_begin, k_end, out=None, stream=None):
     _check(load().tdse_spectrum(_dev_ptr(a, "a"), offs.ctypes.data_as(_i64p), n_rows, float(dt), int(k_begin),
                                 int(k_end), _dev_ptr(out, "S"), _stream_ptr(stream)))
     return out
+
+
+def model_layout(N, dx, softening, dt, charge=1.0, precision=TDSE_FP64, scheme=TDSE_FULL_CN, sm_count=152):
+    """Lanes per instance the cost model picks for such a batch (see tdse_model_layout); no GPU needed."""
+    N = np.atleast_1d(np.asarray(N, dtype=np.int64))
+    n = N.size
+    dx = np.broadcast_to(np.asarray(dx, dtype=np.float64), (n,))
+    a = np.broadcast_to(np.asarray(softening, dtype=np.float64), (n,))
+    Z = np.broadcast_to(np.asarray(charge, dtype=np.float64), (n,))
+    arr = (tdse_instance * n)(*[tdse_instance(int(N[i]), float(dx[i]), float(a[i]), float(Z[i])) for i in range(n)])
+    out = ctypes.c_int32(0)
+    _check(load().tdse_model_layout(arr, n, float(dt), int(precision), int(scheme), int(sm_count), ctypes.byref(out)))
+    return int(out.value)
 
 
 def resample_field(coarse, dt_coarse, dt_fine, n_fine, out=None, out_stride=None, stream=None):

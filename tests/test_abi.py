@@ -84,3 +84,24 @@ def test_package_import_does_not_load_library():
     importlib.reload(paper_2507_04115_gb300)
     from paper_2507_04115_gb300 import inputs
     assert inputs.pulse_steps(4, 0.057, 0.05) == 8818
+
+
+def test_layout_cost_model_on_the_host(lib):
+    """tdse_model_layout runs the planner's cost model without a GPU: the workloads' batches get the
+    layouts the GPU path uses (32 instances per warp when the groups fill the SMs, lanes per instance
+    otherwise), and bad arguments are refused."""
+    from paper_2507_04115_gb300 import inputs, tdse
+    assert tdse.model_layout([4096] * 8192, 0.15, 1.19, 0.02) == 1          # volume batch: 256 groups
+    assert tdse.model_layout([2048] * 1024, 0.15, 1.19, 0.02) == 4          # adjoint batch: 32 -> 128 groups
+    assert tdse.model_layout([2000], 0.2, 1.19, 0.05) == 32                  # single atom
+    assert tdse.model_layout([2000], 0.2, 1.19, 0.05, scheme=tdse.TDSE_NUMEROV_SPLIT) > 1
+    wl = inputs.uneven_batch()
+    assert tdse.model_layout(wl.N, wl.dx, 1.19, wl.dt) == 1                  # 16384 instances in 8 classes
+    # fewer SMs: the same small batch needs fewer lanes to fill them
+    assert tdse.model_layout([2048] * 1024, 0.15, 1.19, 0.02, sm_count=32) == 1
+    # a class whose sweeps cannot be truncated (dt / (4 dx^2) >= 0.85) keeps 32-wide groups
+    assert tdse.model_layout([512], 0.05, 1.19, 0.01) == 1
+    with pytest.raises(tdse.TDSEError):
+        tdse.model_layout([8], 0.2, 1.19, 0.05)
+    with pytest.raises(tdse.TDSEError):
+        tdse.model_layout([512], 0.2, 1.19, 0.05, sm_count=0)
