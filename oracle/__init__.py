@@ -19,6 +19,8 @@ with respect to every field sample).
 ``energy_distribution``: the time-dependent electron energy distribution P(E) of a state through the
 resolvent of the field-free Hamiltonian (Sec. 6.1).
 
+``populations``: the ground-state population and the near-core probability of a state (Sec. 7.5).
+
 ``resample_field``: the input step of Sec. 4.2, a coarsely sampled field moved to t = 0 and
 interpolated to the propagation step by zero-padding its DFT.
 
@@ -167,6 +169,18 @@ def energy_distribution(psi, E_grid, dx, a, eps, Z=1.0, scheme=FULL_CN):
     _check(lib().oracle_energy_distribution(psi.size, dx, a, Z, scheme, psi.view(np.float64).ctypes.data_as(_dp),
                                             _ptr(Eg), Eg.size, eps, _ptr(P)), "oracle_energy_distribution")
     return P
+
+
+def populations(psi, psi0, dx, a, r_core, Z=1.0):
+    """Sec. 7.5's populations of a state psi: the ground-state population |<psi0|psi>|^2 with
+    <u|v> = sum_j conj(u_j) v_j dx (psi0 the normalised field-free ground state), and the
+    probability of finding the electron within |x| < r_core of the nucleus, sum_{|x_j|<r_core} |psi_j|^2 dx."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    psi0 = np.asarray(psi0, dtype=np.complex128)
+    x, _, _ = grid(psi.size, dx, a, Z)
+    ov = np.sum(np.conj(psi0) * psi) * dx
+    core = np.sum(np.abs(psi[np.abs(x) < r_core]) ** 2) * dx
+    return float(np.abs(ov) ** 2), float(core)
 
 
 def resample_field(coarse, dt_coarse, dt_fine, n_fine):

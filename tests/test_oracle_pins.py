@@ -417,3 +417,27 @@ def test_resampling_equals_zero_padded_inverse_fft(oracle_mod):
         ref = np.real(np.fft.ifft(pad)) * L / M
         got = oracle_mod.resample_field(c, dtc, M * dtc / L, L)
         assert np.max(np.abs(got - ref)) < 1e-12
+
+
+# ---------------------------------------------------------------- populations (Sec. 7.5)
+
+def test_populations_of_eigenstates_and_superpositions(oracle_mod):
+    """The ground-state population is 1 for the ground state, 0 for an excited eigenstate, |c0|^2
+    for a superposition c0 u0 + c1 u1 of orthonormal eigenstates (dense diagonalisation of the
+    discrete H0); the near-core probability tends to the norm for a radius beyond the box, and for
+    a Gaussian equals the discrete sum of its closed form."""
+    N, dx, a = 200, 0.25, 1.19
+    w, U = eigh(_dense_h0(oracle_mod, N, dx, a, FULL_CN))
+    u = U / np.sqrt(dx)
+    p0, _ = oracle_mod.populations(u[:, 0], u[:, 0], dx, a, 5.0)
+    assert abs(p0 - 1.0) < 1e-12
+    p1, _ = oracle_mod.populations(u[:, 3], u[:, 0], dx, a, 5.0)
+    assert p1 < 1e-24
+    c0, c1 = 0.6, 0.8j
+    pm, core_all = oracle_mod.populations(c0 * u[:, 0] + c1 * u[:, 1], u[:, 0], dx, a, 1e9)
+    assert abs(pm - 0.36) < 1e-12
+    assert abs(core_all - 1.0) < 1e-12
+    x, _, _ = oracle_mod.grid(N, dx, a)
+    g = np.exp(-x ** 2 / 2) + 0j
+    _, core = oracle_mod.populations(g, u[:, 0], dx, a, 2.0)
+    assert abs(core - np.sum(np.exp(-x[np.abs(x) < 2.0] ** 2)) * dx) < 1e-13
