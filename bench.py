@@ -53,7 +53,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["own", "reference"], default="own")
-    p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large", "resolvent", "field"],
+    p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large", "resolvent", "field",
+                                                "populations"],
                    default="volume",
                    help="volume = the benchmark; the others measure the other workloads (one JSON line each)")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
@@ -536,6 +537,16 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------------------------------- other workloads
 
+def _measured_hbm_gbs():
+    """Measured HBM copy bandwidth of this GPU type in GB/s (MEASURED_PEAKS.json beside this file),
+    else the 6.8 TB/s fallback measured earlier on a GB300."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def _line(metric, value, unit, args, workload, cfg, **extra):
     out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
@@ -668,6 +679,68 @@ def other_workload(args):
               "fine samples/s", args, "%d rows x %d coarse samples (dt %g) -> %d samples (dt %g)" % (n, M, dt_c, n_fine, dt_f),
               dict(rows=n, M=M, dt_coarse=dt_c, dt_fine=dt_f, n_fine=n_fine), dtype="f64",
               fp64_instructions_per_sample=6 * (M // 2 + 1), seconds_per_call=t)
+        return
+
+    if args.workload == "populations":
+        # ground-state population and near-core probability (Sec. 7.5) of the volume batch's states
+        # after a chunk of the pulse.  The kernel reads the rows in the hull of the ground state's
+        # support (tails below 1e-17) and of |x| < r_core; the same rule is applied here to the
+        # ground state to count the bytes it has to read.  Those rows (tens of MB) fit in L2, so
+        # a 512 MB buffer is read before every timed call (a read leaves no dirty lines to write back).
+        wl = inputs.volume_batch()
+        n = wl.n_inst if args.instances <= 0 else min(args.instances, wl.n_inst)
+        N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+        a = softcore.fit_softening(wl.target_energy, N, dx)
+        Nt = 200 if args.nt <= 0 else args.nt
+        E = torch.empty((n, Nt + 1), dtype=torch.float64, device=dev)
+        inputs.sin2_pulse_batch(Nt, dt, wl.E0[:n], float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi[:n], out=E, xp=torch)
+        E = E.reshape(-1).contiguous()
+        b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent), precision=prec)
+        b.ground_state()
+        r_core = 2.0
+        w0 = np.abs(b.get_psi(0).cpu().numpy()) ** 2 * dx
+        thr = 0.5e-34
+        s_lo = int(np.searchsorted(np.cumsum(w0), thr, side="right"))
+        s_hi = N - int(np.searchsorted(np.cumsum(w0[::-1]), thr, side="right"))
+        x = (np.arange(N) - 0.5 * (N - 1)) * dx
+        core = np.nonzero(np.abs(x) < r_core)[0]
+        rows = max(s_hi, int(core[-1]) + 1) - min(s_lo, int(core[0]))
+        d, acc = torch.zeros_like(E), torch.zeros_like(E)
+        b.propagate(E, d, acc)
+        out = torch.empty((n, 2), dtype=torch.float64, device=dev)
+        flush = torch.ones(64 << 20, dtype=torch.float64, device=dev)
+        sink = torch.empty((), dtype=torch.float64, device=dev)
+        for _ in range(max(args.warmup, 3)):
+            b.populations(r_core, out=out)
+        ev = []
+        torch.cuda.synchronize(dev)
+        for _ in range(args.steps):
+            torch.sum(flush, dim=0, out=sink)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.populations(r_core, out=out)
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        t = statistics.mean(e0.elapsed_time(e1) * 1e-3 for e0, e1 in ev)
+        b.close()
+        cx = 16 if prec == tdse.TDSE_FP64 else 8
+        bytes_ = float(n) * rows * cx + 16.0 * n
+        # the FP64 pipe bounds it: two FP64 FMAs per point read (the overlap's real and imaginary
+        # parts), two more per core point; the rows themselves need less time from HBM
+        flops = 4.0 * n * rows + 4.0 * n * int(core.size)
+        peak = FP64_FMA_PER_CLK_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6
+        _line("state populations per second (Sec. 7.5)", n / t, "instance states/s", args,
+              "populations of the volume batch: %d instances, N=%d, r_core=%g, after %d steps" % (n, N, r_core, Nt),
+              dict(instances=n, N=N, r_core=r_core, steps_before=Nt, precision=args.precision, rows_read=rows,
+                   core_rows=int(core.size), l2="512 MB read before every timed call"),
+              dtype="f64 sums", seconds_per_call=t, gpu_launches=args.steps,
+              hbm={"achieved": bytes_ / t / 1e9, "peak": _measured_hbm_gbs(), "unit": "GB/s",
+                   "frac": bytes_ / t / 1e9 / _measured_hbm_gbs(),
+                   "how": "rows_read rows of every state (%d B per point) plus the 16 B result per instance" % cx},
+              roofline={"bound": "alu", "achieved": flops / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                        "frac": flops / t / peak, "traffic": None,
+                        "achieved_how": "2 FP64 FMAs per point of the rows read, 2 more per core point"})
         return
 
     if args.workload == "resolvent":

@@ -175,6 +175,17 @@ tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream)
 tdse_status tdse_energy_distribution(tdse_batch* batch, const double* E_grid_host, int32_t n_energies,
                                      double epsilon, double* P_dev, void* stream);
 
+/* Populations of every instance's current state (Sec. 7.5: the time-dependent ground-state
+ * population and the probability of finding the electron near the nucleus):
+ *     out[2 i]     = | sum_j psi0_j psi_i,j dx |^2        (ground-state population)
+ *     out[2 i + 1] = sum_{|x_j| < r_core} |psi_i,j|^2 dx  (near-core probability)
+ * psi0 is the class's real field-free ground state from the batch's last tdse_ground_state call
+ * (normalised to sum_j psi0_j^2 dx = 1), x_j = (j - (N-1)/2) dx.  r_core >= 0 (+inf gives the
+ * norm).  out_dev: device, n_inst x 2 doubles, row i = instance i in creation order.  Sums run in
+ * FP64 on FP64 and MIXED batches.  TDSE_ERR_STATE before the first tdse_ground_state.
+ * Asynchronous on the stream; allocates nothing (graph-capturable). */
+tdse_status tdse_populations(tdse_batch* batch, double r_core, double* out_dev, void* stream);
+
 /* Field ingestion (Sec. 4.2: the input interval is shifted to start at t = 0 and the coarsely
  * sampled field is interpolated to the propagation step by zero-padding in the Fourier domain).
  * Row r of coarse_dev holds M samples E(t_min + m dt_coarse), m = 0..M-1 (rows contiguous, M

@@ -98,6 +98,7 @@ struct tdse_batch {
     uint32_t wait_polls = 1u << 22;   // MIXED bulk-copy wait bound (tdse_set_wait_limit)
     int sm_count = 0;
     bool initialized = false;
+    bool gs_done = false;             // a ground state was computed (psi0 in d_gs_work)
     // device memory
     ClassDesc* d_cls = nullptr;
     GroupDesc* d_groups = nullptr;
@@ -116,6 +117,7 @@ struct tdse_batch {
     int64_t* d_gs_off = nullptr;
     double* d_gs_energy = nullptr;
     int64_t* d_gs_iters = nullptr;
+    int64_t* d_gs_support = nullptr;   // per class: [lo, hi) outside which psi0 has tail norm < 1e-17
     int64_t psi_elems = 0, scratch_elems = 0;
     // adjoint buffers (allocated on the first tdse_adjoint call, resized when the interval changes)
     void* d_lam = nullptr;
@@ -150,6 +152,7 @@ void free_device(tdse_batch* b)
     cudaFree(b->d_gs_off);
     cudaFree(b->d_gs_energy);
     cudaFree(b->d_gs_iters);
+    cudaFree(b->d_gs_support);
     cudaFree(b->d_lam);
     cudaFree(b->d_ckpt);
     cudaFree(b->d_ckpt_off);
@@ -174,6 +177,7 @@ void free_device(tdse_batch* b)
     b->d_gs_off = nullptr;
     b->d_gs_energy = nullptr;
     b->d_gs_iters = nullptr;
+    b->d_gs_support = nullptr;
 }
 
 // NUMEROV_SPLIT: LU factors of the time-independent A = M2 + i h (-Delta2/2 + M2 V), h = dt/2
@@ -557,6 +561,7 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     if ((e = dev_alloc(&b->d_gs_off, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
     if ((e = dev_alloc(&b->d_gs_energy, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
     if ((e = dev_alloc(&b->d_gs_iters, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
+    if ((e = dev_alloc(&b->d_gs_support, 2 * (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
     if ((e = cudaMemcpy(b->d_cls, b->classes.data(), sizeof(ClassDesc) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->d_gs_off, gs_off.data(), sizeof(int64_t) * n_cls, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemcpy(setup)"));
@@ -697,10 +702,12 @@ tdse_status tdse_ground_state(tdse_batch* b, double dtau, int64_t max_iter, doub
     TDSE_CUDA(launch_ground_state(b->d_cls, n_cls, (int)b->scheme, dtau, max_iter, tol, b->d_gs_work, b->d_gs_off,
                                   b->d_gs_energy, b->d_gs_iters, st),
               "ground_state launch");
+    TDSE_CUDA(launch_gs_support(b->d_cls, n_cls, b->d_gs_work, b->d_gs_off, b->d_gs_support, st), "support launch");
     TDSE_CUDA(launch_broadcast_psi(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->d_gs_work, b->d_gs_off,
                                    b->d_slot_valid, b->d_psi, st),
               "broadcast launch");
     b->initialized = true;
+    b->gs_done = true;
     if (energies_host || iters_host) {
         std::vector<double> e(n_cls);
         std::vector<int64_t> it(n_cls);
@@ -939,6 +946,20 @@ tdse_status tdse_energy_distribution(tdse_batch* b, const double* E_grid_host, i
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     release();
     if (e != cudaSuccess) return cuda_fail(e, "tdse_energy_distribution");
+    return TDSE_OK;
+}
+
+tdse_status tdse_populations(tdse_batch* b, double r_core, double* out_dev, void* stream)
+{
+    if (!b || !out_dev) return fail(TDSE_ERR_ARG, "tdse_populations: NULL argument");
+    if (std::isnan(r_core) || r_core < 0.0) return fail(TDSE_ERR_ARG, "tdse_populations: r_core must be >= 0");
+    if (!b->gs_done) return fail(TDSE_ERR_STATE, "tdse_populations: no ground state (call tdse_ground_state)");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    TDSE_CUDA(launch_populations(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->d_cls,
+                                 b->d_slot_inst, b->d_psi, b->d_gs_work, b->d_gs_off, b->d_gs_support, r_core,
+                                 out_dev, b->sm_count, (cudaStream_t)stream),
+              "populations launch");
     return TDSE_OK;
 }
 

@@ -171,6 +171,21 @@ cudaError_t launch_propagate_numerov(int mixed, const GroupDesc* d_groups, int64
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, double dt,
                                      int* d_busy, int* d_progress, int* d_status, cudaStream_t st);
 
+// Support of each class's ground state (first N doubles of work + work_off[c]): support[2c..2c+1]
+// = [lo, hi), the largest lo and smallest hi with sum_{j<lo} psi0_j^2 dx and sum_{j>=hi} psi0_j^2 dx
+// each at most kSupportTail^2 / 2 (one warp per class).
+constexpr double kSupportTail = 1e-17;
+cudaError_t launch_gs_support(const ClassDesc* d_cls, int n_cls, const double* d_work, const int64_t* d_work_off,
+                              int64_t* d_support, cudaStream_t st);
+
+// Ground-state population and near-core probability of every instance (a cluster of CTAs per
+// group, sized for sm_count SMs), read over the hull of the class's psi0 support and the points
+// with |x_j| < r_core; psi0 of class c: the first N doubles of gs_work + gs_off[c]; out: n_inst x 2.
+cudaError_t launch_populations(int mixed, const GroupDesc* d_groups, int64_t n_groups, const ClassDesc* d_cls,
+                               const int64_t* d_slot_inst, const void* d_psi, const double* d_gs_work,
+                               const int64_t* d_gs_off, const int64_t* d_support, double r_core, double* out,
+                               int sm_count, cudaStream_t st);
+
 cudaError_t launch_get_psi(int mixed, const void* d_psi, int64_t psi_off, int N, int lane, int I, double* out,
                            cudaStream_t st);
 cudaError_t launch_set_psi(int mixed, void* d_psi, int64_t psi_off, int N, int lane, int I, const double* in, cudaStream_t st);

@@ -1,10 +1,12 @@
 // Set-up and auxiliary kernels of libtdse (sm_103a): per-class tables, imaginary-time ground
-// state, wavefunction broadcast and access, and the DFT power spectrum.  The propagation kernels
+// state, wavefunction broadcast and access, the populations of the states, and the DFT power
+// spectrum.  The propagation kernels
 // live in tdse_full_cn.cu and tdse_numerov.cu, the adjoint in tdse_adjoint.cu, the energy
 // distribution in tdse_resolvent.cu.
 #include "tdse_device.cuh"
 #include "tdse_internal.h"
 
+#include <cooperative_groups.h>
 #include <cstdint>
 
 namespace tdse {
@@ -280,6 +282,240 @@ cudaError_t launch_set_psi(int mixed, void* d_psi, int64_t psi_off, int N, int l
         k_set_psi<float2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<float2*>(d_psi), psi_off, N, lane, I, in);
     else
         k_set_psi<double2><<<(N + 255) / 256, 256, 0, st>>>(static_cast<double2*>(d_psi), psi_off, N, lane, I, in);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ populations
+
+// Support of psi0: one warp per class scans 32 points at a time from each end, with an inclusive
+// warp prefix sum of psi0_j^2 dx, and stops at the first point whose running tail exceeds
+// kSupportTail^2 / 2.  The overlap with any psi then misses at most kSupportTail ||psi|| (Cauchy-
+// Schwarz over the two tails), below the rounding of a population.
+__global__ void k_gs_support(const ClassDesc* cls, const double* work, const int64_t* work_off, int64_t* support)
+{
+    const int lane = threadIdx.x & 31;
+    const ClassDesc C = cls[blockIdx.x];
+    const int N = C.N;
+    const double* p0 = work + work_off[blockIdx.x];
+    const double thr = 0.5 * kSupportTail * kSupportTail;
+    int bound[2] = {0, N};
+    for (int side = 0; side < 2; ++side) {
+        double run = 0.0;
+        int found = side == 0 ? N : 0;   // psi0 negligible everywhere: empty support
+        for (int k0 = 0; k0 < N; k0 += kLanes) {
+            const int k = k0 + lane;   // k-th point from this side's end
+            const int j = side == 0 ? k : N - 1 - k;
+            double v = k < N ? p0[j] * p0[j] * C.dx : 0.0;
+            for (int o = 1; o < kLanes; o <<= 1) {
+                const double t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            const unsigned over = __ballot_sync(0xffffffffu, k < N && run + v > thr);
+            if (over) {
+                const int kk = k0 + __ffs(over) - 1;   // first point that must be kept
+                found = side == 0 ? kk : N - kk;
+                break;
+            }
+            run += __shfl_sync(0xffffffffu, v, kLanes - 1);
+        }
+        bound[side] = found;
+    }
+    if (lane == 0) {
+        support[2 * blockIdx.x] = bound[0];
+        support[2 * blockIdx.x + 1] = bound[1] > bound[0] ? bound[1] : bound[0];
+    }
+}
+
+cudaError_t launch_gs_support(const ClassDesc* d_cls, int n_cls, const double* d_work, const int64_t* d_work_off,
+                              int64_t* d_support, cudaStream_t st)
+{
+    if (n_cls == 0) return cudaSuccess;
+    k_gs_support<<<n_cls, kLanes, 0, st>>>(d_cls, d_work, d_work_off, d_support);
+    return cudaGetLastError();
+}
+
+// Ground-state population |sum_j psi0_j psi_j dx|^2 and near-core probability
+// sum_{|x_j| < r_core} |psi_j|^2 dx of every instance (Sec. 7.5).
+//   Only the rows j in the hull of psi0's support [s_lo, s_hi) and of the core interval are read:
+//   outside the support the overlap's terms sum to less than kSupportTail ||psi||, outside the core
+//   interval the second sum has no terms.  The core interval is {j : |x_j| < r_core} with
+//   x_j = (j - (N-1)/2) dx, the same expression (and rounding) as the tables; x is odd about the
+//   centre in floating point too, so the interval is [c_lo, N - c_lo), c_lo found from an estimate
+//   corrected by exact comparisons.
+//   A group is handled by a thread-block cluster of S CTAs (S <= 8, chosen on the host so that the
+//   grid fills the SMs); CTA r of the cluster takes the r-th chunk of the rows.  A warp reads 32
+//   consecutive elements of the [N][I] layout per load (32 / I points of all I instances),
+//   kPopDepth loads in flight per thread; lane l accumulates instance l % I.
+//   Sums: shuffles over the lanes of an instance, the CTA's warps in a fixed order into shared
+//   memory, then CTA 0 of the cluster adds the S CTAs' partials in rank order through distributed
+//   shared memory -- deterministic, no scratch, no atomics.
+constexpr int kPopWarps = 8;
+constexpr int kPopDepth = 4;
+constexpr int kPopMaxCluster = 8;
+
+__device__ __forceinline__ double grid_x(int j, int N, double dx) { return (j - 0.5 * (N - 1)) * dx; }
+
+// float -> double from the IEEE-754 fields with integer operations only (a conversion instruction
+// would occupy the FP64 pipe, which the sums already saturate).  Normal numbers: exponent rebiased
+// by 1023 - 127 = 896, the 23 mantissa bits moved to the top of the 52.  Subnormal floats m 2^-149
+// are normal doubles: with p the position of m's top bit, exponent p - 149 + 1023 and the bits
+// below it as mantissa.  Zero keeps its sign; infinities and NaN (payload kept) map to 2047.
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    const uint32_t p = 31u - (uint32_t)__clz((int)(m | 1u));   // top bit of m (m = 0: unused)
+    const uint32_t E = e == 0xffu ? 2047u : (e != 0u ? e + 896u : (m != 0u ? p + 874u : 0u));
+    const uint32_t M = e != 0u ? m : ((m << (23u - p)) & 0x7fffffu);
+    const uint32_t hi = (u & 0x80000000u) | (E << 20) | (M >> 3);
+    return __hiloint2double((int)hi, (int)(M << 29));
+}
+
+// First j of the core interval; the interval is empty when the result exceeds (N - 1) / 2.
+__device__ int core_lo(int N, double dx, double r_core)
+{
+    const int mid = (N - 1) / 2;   // last point with x <= 0
+    if (!(r_core > 0.0)) return mid + 1;
+    const double t = 0.5 * (N - 1) - r_core / dx;
+    int lo = t <= 0.0 ? 0 : (t >= (double)mid ? mid : (int)ceil(t));
+    while (lo > 0 && fabs(grid_x(lo - 1, N, dx)) < r_core) --lo;
+    while (lo <= mid && !(fabs(grid_x(lo, N, dx)) < r_core)) ++lo;
+    return lo;
+}
+
+template <class Cx>
+__global__ void __launch_bounds__(kPopWarps * 32) k_populations(const GroupDesc* __restrict__ groups,
+                                                                const ClassDesc* __restrict__ cls,
+                                                                const int64_t* __restrict__ slot_inst,
+                                                                const Cx* __restrict__ psi_all,
+                                                                const double* __restrict__ gs_work,
+                                                                const int64_t* __restrict__ gs_off,
+                                                                const int64_t* __restrict__ support, double r_core,
+                                                                double* __restrict__ out)
+{
+    namespace cg = cooperative_groups;
+    __shared__ double part[kPopWarps][3][kLanes];
+    __shared__ double cta_sum[3][kLanes];
+    __shared__ int s_core_lo;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int S = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const GroupDesc G = groups[blockIdx.x / S];
+    const ClassDesc C = cls[G.cls];
+    const int N = G.N, I = G.I, per_warp = kLanes / I;
+    const int i = lane % I, jq = lane / I;
+    // rows to read: hull of the support and the core interval (its bound found by one thread: the
+    // division and the comparisons would otherwise cost every thread as much FP64 work as its sums)
+    if (threadIdx.x == 0) s_core_lo = core_lo(N, C.dx, r_core);
+    __syncthreads();
+    const int c_lo = s_core_lo;
+    const bool core_on = c_lo <= (N - 1) / 2;
+    const int c_hi = N - c_lo;
+    int h_lo = (int)support[2 * G.cls], h_hi = (int)support[2 * G.cls + 1];
+    if (core_on) {
+        h_lo = min(h_lo, c_lo);
+        h_hi = max(h_hi, c_hi);
+    }
+    // chunk of this CTA: whole rows of per_warp points, the first row aligned to per_warp
+    const int r_lo = h_lo / per_warp, r_hi = (h_hi + per_warp - 1) / per_warp;
+    const int chunk_rows = (r_hi - r_lo + S - 1) / S;
+    const int lo = max(h_lo, (r_lo + rank * chunk_rows) * per_warp);
+    const int hi = min(h_hi, (r_lo + (rank + 1) * chunk_rows) * per_warp);
+    const Cx* __restrict__ ps = psi_all + G.psi_off + i;   // point j at ps[j * I]
+    const double* __restrict__ psi0 = gs_work + gs_off[G.cls];
+    const int stride = kPopWarps * per_warp;
+    double ovr = 0.0, ovi = 0.0, core = 0.0;
+    for (int jb = (r_lo + rank * chunk_rows + warp) * per_warp; jb < hi; jb += kPopDepth * stride) {
+        Cx v[kPopDepth];
+        double p0[kPopDepth];
+#pragma unroll
+        for (int u = 0; u < kPopDepth; ++u) {
+            const int j = jb + u * stride + jq;
+            const bool ok = j >= lo && j < hi;
+            v[u] = ok ? ps[(int64_t)j * I] : Cx{0, 0};
+            p0[u] = ok ? psi0[j] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPopDepth; ++u) {
+            ovr = fma(p0[u], to_f64(v[u].x), ovr);
+            ovi = fma(p0[u], to_f64(v[u].y), ovi);
+        }
+    }
+    // the core rows of this chunk once more (from L1/L2): |psi|^2 only where it is summed
+    const int k_lo = max(lo, c_lo), k_hi = min(hi, c_hi);
+    for (int jb = (r_lo + rank * chunk_rows + warp) * per_warp; jb < k_hi; jb += stride) {
+        const int j = jb + jq;
+        if (j >= k_lo && j < k_hi) {
+            const Cx v = ps[(int64_t)j * I];
+            const double vr = to_f64(v.x), vi = to_f64(v.y);
+            core = fma(vr, vr, fma(vi, vi, core));
+        }
+    }
+    for (int o = I; o < kLanes; o <<= 1) {
+        ovr += __shfl_xor_sync(0xffffffffu, ovr, o);
+        ovi += __shfl_xor_sync(0xffffffffu, ovi, o);
+        core += __shfl_xor_sync(0xffffffffu, core, o);
+    }
+    part[warp][0][lane] = ovr;
+    part[warp][1][lane] = ovi;
+    part[warp][2][lane] = core;
+    __syncthreads();
+    if (threadIdx.x < 3 * kLanes) {
+        const int q = threadIdx.x / kLanes, l = threadIdx.x % kLanes;
+        double t = 0.0;
+        for (int w = 0; w < kPopWarps; ++w) t += part[w][q][l];
+        cta_sum[q][l] = t;
+    }
+    cluster.sync();   // every CTA's partials are visible to the cluster
+    if (rank == 0 && threadIdx.x < I) {
+        double sr = 0.0, si = 0.0, sc = 0.0;
+        for (int r = 0; r < S; ++r) {
+            const double* rs = cluster.map_shared_rank(&cta_sum[0][0], r);
+            sr += rs[0 * kLanes + i];
+            si += rs[1 * kLanes + i];
+            sc += rs[2 * kLanes + i];
+        }
+        const int64_t inst = slot_inst[G.slot0 + i];
+        if (inst >= 0) {
+            const double dx = C.dx;
+            out[2 * inst] = (sr * sr + si * si) * (dx * dx);
+            out[2 * inst + 1] = sc * dx;
+        }
+    }
+    cluster.sync();   // the partials stay alive until CTA 0 has read them
+}
+
+cudaError_t launch_populations(int mixed, const GroupDesc* d_groups, int64_t n_groups, const ClassDesc* d_cls,
+                               const int64_t* d_slot_inst, const void* d_psi, const double* d_gs_work,
+                               const int64_t* d_gs_off, const int64_t* d_support, double r_core, double* out,
+                               int sm_count, cudaStream_t st)
+{
+    if (n_groups == 0) return cudaSuccess;
+    if (n_groups > (int64_t(1) << 27)) return cudaErrorInvalidValue;
+    // CTAs per group: enough for about 8 resident CTAs of 8 warps per SM
+    const int64_t want = (int64_t)std::max(sm_count, 1) * 8;
+    const int S = (int)std::min<int64_t>(kPopMaxCluster, std::max<int64_t>(1, (want + n_groups - 1) / n_groups));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_groups * S));
+    cfg.blockDim = dim3(kPopWarps * 32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (mixed)
+        e = cudaLaunchKernelEx(&cfg, k_populations<float2>, d_groups, d_cls, d_slot_inst,
+                               static_cast<const float2*>(d_psi), d_gs_work, d_gs_off, d_support, r_core, out);
+    else
+        e = cudaLaunchKernelEx(&cfg, k_populations<double2>, d_groups, d_cls, d_slot_inst,
+                               static_cast<const double2*>(d_psi), d_gs_work, d_gs_off, d_support, r_core, out);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

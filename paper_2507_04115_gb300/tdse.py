@@ -22,6 +22,7 @@ _lib = None
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
            "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_model_layout",
+           "tdse_populations",
            "tdse_last_error")
 
 
@@ -103,6 +104,7 @@ def load(path: str | None = None):
     L.tdse_resample_field.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int, _vp]
     L.tdse_energy_distribution.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp]
+    L.tdse_populations.argtypes = [_vp, ctypes.c_double, _vp, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -263,6 +265,15 @@ class Batch:
             out = torch.empty((self.n_inst, Eg.size), dtype=torch.float64, device=torch.device("cuda", self.device))
         _check(load().tdse_energy_distribution(self._h, Eg.ctypes.data_as(_dp), int(Eg.size), float(epsilon),
                                                _dev_ptr(out, "P"), _stream_ptr(stream)))
+        return out
+
+    def populations(self, r_core, out=None, stream=None):
+        """[i, 0]: ground-state population of instance i's current state, [i, 1]: its probability
+        within |x| < r_core (see tdse_populations); a float64 device tensor n_inst x 2."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n_inst, 2), dtype=torch.float64, device=torch.device("cuda", self.device))
+        _check(load().tdse_populations(self._h, float(r_core), _dev_ptr(out, "out"), _stream_ptr(stream)))
         return out
 
     def set_wait_limit(self, polls=1 << 22):
