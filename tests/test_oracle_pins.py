@@ -433,7 +433,7 @@ def test_populations_of_eigenstates_and_superpositions(oracle_mod):
     assert abs(p0 - 1.0) < 1e-12
     p1, _ = oracle_mod.populations(u[:, 3], u[:, 0], dx, a, 5.0)
     assert p1 < 1e-24
-    c0, c1 = 0.6, 0.8j
+    c0, c1 = 0.6 * np.exp(1j * np.pi / 3), 0.8j   # complex c0: |<u0|psi>|^2, not Re(<u0|psi>)^2
     pm, core_all = oracle_mod.populations(c0 * u[:, 0] + c1 * u[:, 1], u[:, 0], dx, a, 1e9)
     assert abs(pm - 0.36) < 1e-12
     assert abs(core_all - 1.0) < 1e-12
@@ -441,3 +441,11 @@ def test_populations_of_eigenstates_and_superpositions(oracle_mod):
     g = np.exp(-x ** 2 / 2) + 0j
     _, core = oracle_mod.populations(g, u[:, 0], dx, a, 2.0)
     assert abs(core - np.sum(np.exp(-x[np.abs(x) < 2.0] ** 2)) * dx) < 1e-13
+    # the core region is open: on an odd grid x = +-2 are grid points (x_j = (j - 100) dx) and are
+    # left out; a unit spike there and nowhere else has no near-core probability at r = 2
+    x1, _, _ = oracle_mod.grid(201, dx, a)
+    spike = np.zeros(201, dtype=complex)
+    spike[[92, 108]] = 1.0
+    assert x1[108] == 2.0 and x1[92] == -2.0
+    assert oracle_mod.populations(spike, np.zeros(201), dx, a, 2.0)[1] == 0.0
+    assert abs(oracle_mod.populations(spike, np.zeros(201), dx, a, 2.0 + 1e-12)[1] - 2 * dx) < 1e-15
