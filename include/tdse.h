@@ -182,7 +182,8 @@ tdse_status tdse_energy_distribution(tdse_batch* batch, const double* E_grid_hos
  * psi0 is the class's real field-free ground state from the batch's last tdse_ground_state call
  * (normalised to sum_j psi0_j^2 dx = 1), x_j = (j - (N-1)/2) dx.  r_core >= 0 (+inf gives the
  * norm).  out_dev: device, n_inst x 2 doubles, row i = instance i in creation order.  Sums run in
- * FP64 on FP64 and MIXED batches.  TDSE_ERR_STATE before the first tdse_ground_state.
+ * FP64 on FP64 and MIXED batches.  TDSE_ERR_STATE before the first tdse_ground_state, and after a
+ * tdse_set_layout until a state is set again.
  * Asynchronous on the stream; allocates nothing (graph-capturable). */
 tdse_status tdse_populations(tdse_batch* batch, double r_core, double* out_dev, void* stream);
 

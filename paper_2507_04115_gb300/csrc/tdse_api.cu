@@ -954,6 +954,7 @@ tdse_status tdse_populations(tdse_batch* b, double r_core, double* out_dev, void
     if (!b || !out_dev) return fail(TDSE_ERR_ARG, "tdse_populations: NULL argument");
     if (std::isnan(r_core) || r_core < 0.0) return fail(TDSE_ERR_ARG, "tdse_populations: r_core must be >= 0");
     if (!b->gs_done) return fail(TDSE_ERR_STATE, "tdse_populations: no ground state (call tdse_ground_state)");
+    if (!b->initialized) return fail(TDSE_ERR_STATE, "tdse_populations: no state (the layout changed since)");
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
     TDSE_CUDA(launch_populations(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->d_cls,

@@ -86,6 +86,36 @@ def test_populations_need_a_ground_state(env):
     b.ground_state(dtau=0.1, max_iter=10, tol=0.0)
     with pytest.raises(tdse.TDSEError):
         b.populations(-1.0)
+    with pytest.raises(tdse.TDSEError):
+        b.populations(float("nan"))
+    b.populations(1.0)
+    b.set_layout(8)   # discards the state
+    with pytest.raises(tdse.TDSEError):
+        b.populations(1.0)
+    b.close()
+
+
+def test_populations_one_cta_per_group(env):
+    """1300 one-instance groups: more groups than the grid target, so every cluster is a single
+    CTA; sampled instances against the oracle."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    rng = np.random.default_rng(29)
+    n, N, dx, a, dt = 1300, 160, 0.25, 1.2, 0.05
+    nt = 120
+    E = np.concatenate([inputs.sin2_pulse(nt, dt, rng.uniform(0.05, 0.2), 0.057, 1.0, rng.uniform(0, 6))
+                        for _ in range(n)])
+    Et = torch.from_numpy(E).to("cuda")
+    b = tdse.Batch([N] * n, dx, a, [nt] * n, dt, absorber=(8.0, 0.125), lanes_per_instance=32)
+    b.ground_state(**GS_KW)
+    d, acc = torch.zeros_like(Et), torch.zeros_like(Et)
+    b.propagate(Et, d, acc)
+    pop = b.populations(1.5).cpu().numpy()
+    psi0 = oracle.ground_state(N, dx, a, **GS_KW)[0]
+    for i in [0, 1, n - 1] + list(rng.integers(0, n, 20)):
+        ref = oracle.populations(b.get_psi(int(i)).cpu().numpy(), psi0, dx, a, 1.5)
+        assert abs(pop[i, 0] - ref[0]) < 1e-10, i
+        assert abs(pop[i, 1] - ref[1]) < 1e-12, i
     b.close()
 
 
