@@ -129,7 +129,7 @@ def gaussian_beam_volume(n_r=64, n_z=128, lam_nm=800.0, n_cycles=10, N=4096, dx=
     wz = w0_m * np.sqrt(1.0 + (Zc / zR_m) ** 2)
     inten = i0_w_cm2 * (w0_m / wz) ** 2 * np.exp(-2.0 * R ** 2 / wz ** 2)
     k = 2.0 * np.pi / (lam_nm * 1e-9)
-    with np.errstate(divide="ignore"):
+    with np.errstate(divide="ignore", invalid="ignore"):
         curv = np.where(Zc == 0.0, 0.0, k * R ** 2 / (2.0 * Zc * (1.0 + (zR_m / np.where(Zc == 0.0, 1.0, Zc)) ** 2)))
     phi = -np.arctan(Zc / zR_m) + curv
     amp = field_from_intensity(inten).ravel() * rng.uniform(1.0 - noise, 1.0 + noise, n_r * n_z)
