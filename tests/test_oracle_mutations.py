@@ -12,8 +12,6 @@ import shutil
 import subprocess
 import sys
 
-import pytest
-
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 C_SRC = "tdse_oracle.c"
 PY_SRC = "__init__.py"
@@ -53,14 +51,35 @@ MUTANTS = [
      "        blo[j] = M[0][j] - c * K[0][j]; bdi[j] = M[1][j] - c * K[1][j]; bup[j] = M[2][j] + c * K[2][j];\n"
      "    }\n    for (int j = 0; j < N; ++j) psi[j] = exp", "ground state: sign in the explicit half-step"),
     (C_SRC, "gE[n] += 0.5 * gbar;", "gE[n] += gbar;", "adjoint: midpoint split of the field gradient"),
+    (C_SRC, "lam[j] = 2.0 * dx * (gd[Nt] * x[j] + ga[Nt] * (dV[j] + E[Nt])) * p[j];",
+     "lam[j] = 2.0 * dx * (gd[Nt] * x[j] + ga[Nt] * dV[j]) * p[j];", "adjoint: field dropped from the terminal source"),
+    (C_SRC, "if (creal(psi[N / 2]) < 0.0)", "if (creal(psi[N / 2]) > 0.0)", "ground state: sign convention"),
     (C_SRC, "tri_solve(N, blo, bdi, bup, r, mu, work);", "tri_solve(N, lo, di, up, r, mu, work);",
      "adjoint: A_n instead of its adjoint B_n"),
     (C_SRC, "const double norm = 1.0 / (3.14159265358979323846 * eps);", "const double norm = 1.0 / eps;",
      "energy distribution: N_eps"),
     (C_SRC, "tri_apply(N, mlo, mdi, mup, psi, r);                         /* M psi */",
      "memcpy(r, psi, sizeof(double complex) * N);", "energy distribution: M dropped from the right-hand side"),
+    (C_SRC, "lo[j] = z * M[0][j] - K[0][j];", "lo[j] = z * M[0][j] + K[0][j];",
+     "energy distribution: sign of K's sub-diagonal"),
+    (C_SRC, "if (j > 0) s += lo[j] * v[j - 1];", "if (j > 0) s += up[j] * v[j - 1];",
+     "tridiagonal product: transposed operand"),
+    (C_SRC, "m[j] = (c > 0.0) ? pow(c, exponent) : 0.0;", "m[j] = (c > 0.0) ? c : 0.0;", "mask: exponent ignored"),
+    (C_SRC, "double xb = 0.5 * N * dx - width;", "double xb = 0.5 * (N - 1) * dx - width;",
+     "mask: plateau edge off by half a cell"),
+    (C_SRC, "tri_solve(N, lo, di, up, t1, t2, work);", "memcpy(t2, t1, sizeof(double complex) * N);",
+     "NUMEROV energy: M2^-1 dropped"),
+    (C_SRC, "sn += rho;", "sn += 1.0;", "observables: norm sum"),
+    (C_SRC, "const double complex c = I * 0.5 * dt;", "const double complex c = I * dt;", "propagation: h = dt"),
+    (C_SRC, "nrm = sqrt(nrm * dx);", "nrm = sqrt(nrm);", "ground state: normalisation without dx"),
+    (C_SRC, "gE[Nt] += ga[Nt] * dx * nrm;", "gE[Nt] += 0.0 * nrm;", "adjoint: terminal direct field term"),
     (PY_SRC, "return np.abs(np.fft.fft(acc)) ** 2 * dt * dt", "return np.abs(np.fft.fft(acc)) ** 2 * dt",
      "spectrum: dt^2"),
+    (PY_SRC, "return np.abs(np.fft.fft(acc)) ** 2 * dt * dt", "return np.abs(np.fft.ifft(acc)) ** 2 * dt * dt",
+     "spectrum: inverse transform"),
+    (PY_SRC, "coef = w * Eh[k % M] / M", "coef = w * Eh[k % M]", "field ingestion: 1/M"),
+    (PY_SRC, "t = np.arange(n_fine) * dt_fine", "t = np.arange(1, n_fine + 1) * dt_fine",
+     "field ingestion: time origin"),
     (PY_SRC, "        w[0] = w[-1] = 0.5\n", "        pass\n", "field ingestion: Nyquist bin not split"),
     (PY_SRC, "ov = np.sum(np.conj(psi0) * psi) * dx", "ov = np.sum(np.conj(psi0) * psi)", "populations: dx missing"),
     (PY_SRC, "psi[np.abs(x) < r_core]", "psi[np.abs(x) <= r_core]", "populations: closed core interval"),

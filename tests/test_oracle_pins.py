@@ -140,6 +140,7 @@ def test_ground_state_matches_dense_eigensolver(oracle_mod, scheme):
     w, U = eigh(H)
     psi, e, it = oracle_mod.ground_state(N, dx, a, scheme=scheme, tol=1e-15, max_iter=20000)
     assert abs(e - w[0]) < 1e-12
+    assert psi[N // 2].real > 0 and np.all(np.abs(psi.imag) == 0)   # reading GS: real, positive at the centre
     u = U[:, 0] / np.sqrt(dx)
     overlap = abs(np.sum(np.conj(psi) * u) * dx)
     assert overlap > 1 - 1e-12
@@ -326,6 +327,38 @@ def test_adjoint_matches_central_differences(oracle_mod):
     eps = 1e-6
     fd = (loss(E + eps * v) - loss(E - eps * v)) / (2 * eps)
     assert abs(fd - np.dot(gE, v)) < 1e-6 * abs(fd)
+
+
+def test_adjoint_with_strong_absorption(oracle_mod):
+    """A packet running into the absorber (the norm falls to 1 %), loss = a at the last sample with a
+    large final field: dL/dE_k then goes mostly through E_Nt times the norm's dependence on E_k,
+    which the unitary part cannot see.  Central differences at several samples."""
+    N, dx, dt, a = 300, 0.2, 0.05, 1.19
+    nt = 160
+    x, _, _ = oracle_mod.grid(N, dx, a)
+    psi0 = np.exp(-(x - 14.0) ** 2 / 4.0 + 2.0j * x)
+    psi0 /= np.sqrt(np.sum(np.abs(psi0) ** 2) * dx)
+    rng = np.random.default_rng(11)
+    E = 0.05 * rng.standard_normal(nt + 1)
+    E[-1] = 0.4
+    m = oracle_mod.mask(N, dx, 15.0, 0.125)
+    gd = np.zeros(nt + 1)
+    ga = np.zeros(nt + 1)
+    ga[-1] = 1.0
+
+    def loss(Ev):
+        return float(oracle_mod.propagate(psi0, Ev, dx, dt, a, mask_values=m)[2][-1])
+
+    psi_end = oracle_mod.propagate(psi0, E, dx, dt, a, mask_values=m)[0]
+    assert _norm(psi_end, dx) < 0.02
+    gE = oracle_mod.adjoint(psi0, E, dx, dt, a, gd, ga, mask_values=m)
+    for k in [0, 40, 100, 159, 160]:
+        eps = 1e-5
+        Ep, Em = E.copy(), E.copy()
+        Ep[k] += eps
+        Em[k] -= eps
+        fd = (loss(Ep) - loss(Em)) / (2 * eps)
+        assert abs(fd - gE[k]) < 1e-6 * (abs(fd) + 1e-3), (k, fd, gE[k])
 
 
 # ---------------------------------------------------------------- energy distribution (Sec. 6.1)
