@@ -73,6 +73,21 @@ MUTANTS = [
     (C_SRC, "const double complex c = I * 0.5 * dt;", "const double complex c = I * dt;", "propagation: h = dt"),
     (C_SRC, "nrm = sqrt(nrm * dx);", "nrm = sqrt(nrm);", "ground state: normalisation without dx"),
     (C_SRC, "gE[Nt] += ga[Nt] * dx * nrm;", "gE[Nt] += 0.0 * nrm;", "adjoint: terminal direct field term"),
+    (C_SRC, "num += conj(psi[j]) * (t2[j] + V[j] * psi[j]);", "num += conj(psi[j]) * t2[j];",
+     "energy: potential dropped"),
+    (C_SRC, "lo[j] = -0.5 * inv_dx2; di[j] = inv_dx2; up[j] = -0.5 * inv_dx2; }",
+     "lo[j] = -0.5 * inv_dx2; di[j] = 2.0 * inv_dx2; up[j] = -0.5 * inv_dx2; }", "energy: kinetic diagonal"),
+    (C_SRC, "if (d && acc) observables(N, dx, x, dV, E[n + 1], psi, &d[n + 1], &acc[n + 1]);",
+     "if (d && acc) observables(N, dx, x, dV, E[n], psi, &d[n + 1], &acc[n + 1]);", "observables: field time level"),
+    (C_SRC, "gbar += x[j] * cimag(conj(mu[j]) * (p[j] + q[j]));", "gbar += x[j] * cimag(conj(mu[j]) * (p[j] - q[j]));",
+     "adjoint: sign of the new state in the field gradient"),
+    (C_SRC, "for (int j = 0; j < N; ++j) r[j] = (mask ? mask[j] : 1.0) * lam[j];",
+     "for (int j = 0; j < N; ++j) r[j] = lam[j];", "adjoint: mask dropped from the backward step"),
+    (PY_SRC, "diag = inv + (10.0 / 12.0) * (V - sigma)", "diag = inv + (V - sigma)",
+     "Numerov eigenvalue: M2 weight of the diagonal"),
+    (PY_SRC, "lowest_eigenvalue(N, dx, a, Z, scheme) - target", "lowest_eigenvalue(N, dx, a, Z, scheme) + target",
+     "soft-core fit: sign of the target"),
+    (PY_SRC, "w = eigh_tridiagonal(inv + V,", "w = eigh_tridiagonal(inv + 0.5 * V,", "FD eigenvalue: potential weight"),
     (PY_SRC, "return np.abs(np.fft.fft(acc)) ** 2 * dt * dt", "return np.abs(np.fft.fft(acc)) ** 2 * dt",
      "spectrum: dt^2"),
     (PY_SRC, "return np.abs(np.fft.fft(acc)) ** 2 * dt * dt", "return np.abs(np.fft.ifft(acc)) ** 2 * dt * dt",
