@@ -95,13 +95,15 @@ def test_populations_need_a_ground_state(env):
     b.close()
 
 
-def test_populations_one_cta_per_group(env):
-    """1300 one-instance groups: more groups than the grid target, so every cluster is a single
-    CTA; sampled instances against the oracle."""
+@pytest.mark.parametrize("n", [250, 1300])
+def test_populations_many_groups(env, n):
+    """One-instance groups: 250 give clusters of 5 CTAs (the volume benchmark's shape, 256 groups),
+    1300 exceed the grid target so every cluster is a single CTA; sampled instances against the
+    oracle."""
     tdse, oracle = env
     from paper_2507_04115_gb300 import inputs
     rng = np.random.default_rng(29)
-    n, N, dx, a, dt = 1300, 160, 0.25, 1.2, 0.05
+    N, dx, a, dt = 160, 0.25, 1.2, 0.05
     nt = 120
     E = np.concatenate([inputs.sin2_pulse(nt, dt, rng.uniform(0.05, 0.2), 0.057, 1.0, rng.uniform(0, 6))
                         for _ in range(n)])
