@@ -176,6 +176,11 @@ class Batch:
         self.row_offsets = np.ascontiguousarray(row_offsets, dtype=np.int64)
         self.N = N
         self.dx = np.array(dx)
+        self.softening = np.array(a)
+        self.charge = np.array(Z)
+        self.precision = int(precision)
+        self.scheme = int(scheme)
+        self.lanes_per_instance = 0          # 0 = the planner's cost model (see set_layout)
         self.dt = float(dt)
         self.device = int(device)
         self.n_inst = n
@@ -283,6 +288,7 @@ class Batch:
     def set_layout(self, lanes_per_instance=0):
         """Lanes per instance of the layout (see tdse_set_layout; 0 = cost model).  Discards the state."""
         _check(load().tdse_set_layout(self._h, int(lanes_per_instance)))
+        self.lanes_per_instance = int(lanes_per_instance)
 
     def save_state(self, stream=None):
         """Device copy of every wavefunction (opaque layout; see tdse_copy_state)."""
