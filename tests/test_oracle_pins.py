@@ -260,6 +260,36 @@ def test_schemes_agree_to_discretisation_error(oracle_mod):
     assert gaps[0] / gaps[1] > 2.0
 
 
+# ---------------------------------------------------------------- harmonic cutoff (Sec. 7.1)
+
+def test_harmonic_cutoff_law(oracle_mod):
+    """The single-atom configuration (800 nm, 4-cycle sin^2, 1e14 W/cm^2, E_g = -0.579) gives a
+    harmonic plateau that ends near the semi-classical cutoff q_cut = (I_p + 3.17 U_p)/w = 22.4
+    (Sec. 7.1), U_p = E0^2/(4 w^2): the yield first drops below 1 % of the plateau within ten orders
+    above q_cut and is down by 1e5 at q ~ 35-41.  A wrong field coupling moves or removes the
+    cutoff."""
+    from paper_2507_04115_gb300 import inputs
+    wl = inputs.single_atom()
+    N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+    w, E0 = float(wl.omega[0]), float(wl.E0[0])
+    a = oracle_mod.fit_softening(-0.579, N, dx)
+    psi0, _, _ = oracle_mod.ground_state(N, dx, a, tol=1e-12)
+    _, _, acc = oracle_mod.propagate(psi0, wl.field_rows()[0], dx, dt, a,
+                                     mask_values=oracle_mod.mask(N, dx, 20.0, 0.125))
+    S = oracle_mod.spectrum(acc * np.hanning(acc.size), dt)
+    q = 2 * np.pi * np.arange(acc.size) / (acc.size * dt) / w
+
+    def band(q0):
+        return S[np.abs(q - q0) < 0.5].sum()
+
+    q_cut = (0.579 + 3.17 * E0 ** 2 / (4 * w ** 2)) / w
+    assert abs(q_cut - 22.4) < 0.1
+    plateau = np.mean([band(k) for k in range(11, 22, 2)])
+    assert plateau > 1e5 * np.mean([band(k) for k in range(35, 42, 2)])
+    drop = next(k for k in range(11, 61, 2) if band(k) < 1e-2 * plateau)
+    assert q_cut <= drop <= q_cut + 10, drop
+
+
 # ---------------------------------------------------------------- mask and spectrum
 
 def test_mask_shape(oracle_mod):
