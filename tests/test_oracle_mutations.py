@@ -111,6 +111,11 @@ def _make_copy(dest, mutant):
     os.makedirs(os.path.join(dest, "tests"))
     for f in PIN_FILES:
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dest, "tests", f))
+    # the seeded input generators some pins draw their workloads from (no method arithmetic)
+    pkg = "paper_2507_04115_gb300"
+    os.makedirs(os.path.join(dest, pkg))
+    for f in ("__init__.py", "inputs.py"):
+        shutil.copy(os.path.join(ROOT, pkg, f), os.path.join(dest, pkg, f))
     if mutant is not None:
         fname, old, new, _ = mutant
         path = os.path.join(dest, "oracle", fname)
