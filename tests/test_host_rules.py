@@ -64,3 +64,42 @@ def test_planning_rules(tmp_path):
                            str(src), "-o", str(exe)])
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-3000:]
+
+
+RING_PROGRAM = r"""
+#include <cstdio>
+#include "tdse_sched.cuh"
+using namespace tdse;
+int main() {
+    int bad = 0;
+    for (int P = 1; P <= kMaxSegments; ++P)
+        for (int per_sm = 1; per_sm <= 4; ++per_sm) {
+            const int r = full_cn_ring_slots(P, per_sm);
+            if (r < kMinRing || r > kMaxRing) { std::printf("P %d per_sm %d: ring %d\n", P, per_sm, r); ++bad; }
+            // more slots only when they fit: per_sm CTAs of this size share 220 KB
+            if (r > kMinRing && (size_t)per_sm * full_cn_smem_bytes(1, P, r) > 220u * 1024u) {
+                std::printf("P %d per_sm %d: %zu bytes x %d\n", P, per_sm, full_cn_smem_bytes(1, P, r), per_sm); ++bad;
+            }
+            if (r < kMaxRing && (size_t)per_sm * full_cn_smem_bytes(1, P, r + 1) <= 220u * 1024u) {
+                std::printf("P %d per_sm %d: ring %d could be deeper\n", P, per_sm, r); ++bad;
+            }
+        }
+    // one CTA of any width fits the 227 KB a CTA may use
+    if (full_cn_smem_max_bytes() > 227u * 1024u) { std::printf("max %zu\n", full_cn_smem_max_bytes()); ++bad; }
+    std::printf("%d violations\n", bad);
+    return bad ? 1 : 0;
+}
+"""
+
+
+def test_mixed_ring_depth_fits_shared_memory(tmp_path):
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("needs nvcc")
+    src = tmp_path / "ring.cu"
+    src.write_text(RING_PROGRAM)
+    exe = tmp_path / "ring"
+    subprocess.check_call([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC,
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-3000:]
