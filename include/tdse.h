@@ -51,7 +51,8 @@ typedef enum {
     TDSE_ERR_CUDA = 2,       /* a CUDA runtime call failed */
     TDSE_ERR_NONFINITE = 3,  /* an instance's norm became non-finite or grew above 1 + 1e-6 (FP64),
                                 1 + 1e-3 (MIXED) */
-    TDSE_ERR_TIMEOUT = 4,    /* reserved: a bounded device wait gave up */
+    TDSE_ERR_TIMEOUT = 4,    /* a bounded device wait gave up (MIXED bulk copies, see
+                                tdse_set_wait_limit); reported by tdse_check */
     TDSE_ERR_NOMEM = 5,      /* device or host allocation failed */
     TDSE_ERR_STATE = 6       /* call out of order (e.g. propagate before any initial state) */
 } tdse_status;
@@ -154,7 +155,8 @@ tdse_status tdse_adjoint(tdse_batch* batch, const double* E_dev, const double* g
 
 /* Synchronise the stream and report TDSE_ERR_NONFINITE if any instance's norm became non-finite
  * or exceeded 1 + 1e-6 (FP64; 1 + 1e-3 in MIXED) during a propagation since the batch was created
- * or last checked;
+ * or last checked, or TDSE_ERR_TIMEOUT if a bounded bulk-copy wait gave up for it (MIXED, see
+ * tdse_set_wait_limit);
  * *first_bad_host (may be NULL) receives the first such instance or -1.  Clears the flags. */
 tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream);
 
