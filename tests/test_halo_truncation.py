@@ -66,3 +66,52 @@ def test_segments_match_the_exact_solve_at_the_rule_halo():
         # a halo of 5 rows leaves errors near beta^5 ~ 5e-4
         ys5 = np.concatenate([_segment_solve(off, di, off, r, w * m, min(N, (w + 1) * m), 5) for w in range(P)])
         assert np.max(np.abs(ys5 - y)) > 1e-6 * np.max(np.abs(y))
+
+
+def test_numerov_substitutions_with_exact_factors():
+    """NUMEROV_SPLIT factors its constant A = M2 + i h (-Delta2/2 + M2 V) once over the whole grid;
+    the kernels truncate only the two substitutions, whose errors shrink by |L_j| and |C_j| per
+    row, so the halo comes from rho = max_j max(|L_j|, |C_j|)."""
+    N, dx, dt, a = 4096, 0.15, 0.02, 1.19
+    x = (np.arange(N) - 0.5 * (N - 1)) * dx
+    V = -1.0 / np.sqrt(x * x + a * a)
+    h = 0.5 * dt
+    lo_c = 1 / 12 + 1j * h * (-0.5 / dx ** 2 + np.concatenate([[0.0], V[:-1]]) / 12)   # A[j, j-1]
+    up_c = 1 / 12 + 1j * h * (-0.5 / dx ** 2 + np.concatenate([V[1:], [0.0]]) / 12)    # A[j, j+1]
+    di = 10 / 12 + 1j * h * (1.0 / dx ** 2 + 10 / 12 * V)
+    # exact factors over the whole grid, scaled as the kernels store them: pivots p_j,
+    # L_j = A[j, j-1] / p_j, C_j = A[j, j+1] / p_j
+    p = np.empty(N, dtype=complex)
+    p[0] = di[0]
+    for j in range(1, N):
+        p[j] = di[j] - lo_c[j] * up_c[j - 1] / p[j - 1]
+    L = np.zeros(N, dtype=complex)
+    L[1:] = lo_c[1:] / p[1:]
+    C = up_c / p
+    rho = max(np.max(np.abs(L)), np.max(np.abs(C[:-1])))
+    K = _halo(rho)
+    assert rho < 0.85
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    ab = np.zeros((3, N), dtype=complex)
+    ab[0, 1:] = up_c[:-1]
+    ab[1] = di
+    ab[2, :-1] = lo_c[1:]
+    y = solve_banded((1, 1), ab, r)
+
+    def seg(lo, hi, K):
+        a0, b0 = max(0, lo - K), min(N, hi + K)
+        z = np.zeros(b0 - a0, dtype=complex)              # forward: z_j = r_j / p_j - L_j z_{j-1}
+        for k, j in enumerate(range(a0, b0)):
+            z[k] = r[j] / p[j] - (L[j] * z[k - 1] if k > 0 else 0.0)
+        u = np.zeros(b0 - a0, dtype=complex)              # back: u_j = z_j - C_j u_{j+1}
+        for k in range(b0 - a0 - 1, -1, -1):
+            u[k] = z[k] - (C[a0 + k] * u[k + 1] if k + 1 < b0 - a0 else 0.0)
+        return u[lo - a0: hi - a0]
+
+    P = 12
+    m = -(-N // P)
+    ys = np.concatenate([seg(w * m, min(N, (w + 1) * m), K) for w in range(P)])
+    assert np.max(np.abs(ys - y)) < 1e-14 * np.max(np.abs(y))
+    ys5 = np.concatenate([seg(w * m, min(N, (w + 1) * m), 5) for w in range(P)])
+    assert np.max(np.abs(ys5 - y)) > 1e-6 * np.max(np.abs(y))
