@@ -177,10 +177,22 @@ def spectral_errors(S, S_ref, omega0, dt, L, q_cut):
 
 
 def _oracle_job(args):
+    """One oracle propagation in a worker process; returns (a(t), the worker's own seconds for it)."""
     import oracle
     (psi0, E, dx, dt, a, mask, n_end) = args
+    t0 = time.perf_counter()
     _, d, acc = oracle.propagate(psi0, E, dx, dt, a, mask_values=mask, n_begin=0, n_end=n_end)
-    return acc
+    return acc, time.perf_counter() - t0
+
+
+def _cpu_baseline_line(n_jobs, N, steps, secs, cores, sample):
+    """Oracle throughput from the workers' own timers: every job ran in its own process on its own
+    core, started together, so the sample took max(secs) of wall time on `cores` cores."""
+    pts = float(N) * steps
+    return {"value": n_jobs * pts / max(secs), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "per_core": statistics.mean(pts / s for s in secs), "sample": sample,
+            "how": "sum of the sample's grid-point steps / the slowest worker's own perf_counter time around "
+                   "oracle.propagate; per_core = mean over workers of their own rate"}
 
 
 def run_oracle_pool(jobs, workers):
@@ -226,7 +238,6 @@ def own_arm(args):
     cpu_pool = cpu_async = None
     cores = 0
     sample_idx = []
-    t_cpu0 = None
     if args.cpu_baseline and rank == 0 and world == 1:
         cores = args.cpu_instances or min(16, os.cpu_count() or 1)
         sample_idx = list(inputs.subsample(n, cores, 101))
@@ -241,7 +252,6 @@ def own_arm(args):
         jobs = [(psi0_o, inputs.sin2_pulse(Nt, dt, E0[i], omega, ncyc, phi[i]), dx, dt, a_soft, m, Nt)
                 for i in sample_idx]
         cpu_pool = run_oracle_pool(jobs, cores)
-        t_cpu0 = time.time()
         cpu_async = cpu_pool.map_async(_oracle_job, jobs, chunksize=1)
 
     offs = np.arange(n + 1, dtype=np.int64) * (S + 1)
@@ -372,14 +382,14 @@ def own_arm(args):
     cpu_baseline = None
     spec_err = None
     if cpu_async is not None:
-        accs = cpu_async.get()
-        t_cpu = time.time() - t_cpu0
+        res = cpu_async.get()
         cpu_pool.close()
         cpu_pool.join()
-        cpu_pts = float(len(sample_idx)) * N * Nt
-        cpu_baseline = {"value": cpu_pts / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-                        "sample": "%d instances of this workload (seeded subsample), full %d-step propagation each, "
-                                  "one spawned process per core, while the GPU ran" % (len(sample_idx), Nt)}
+        accs = [r[0] for r in res]
+        secs = [r[1] for r in res]
+        cpu_baseline = _cpu_baseline_line(len(sample_idx), N, Nt, secs, cores,
+                                          "%d instances of this workload (seeded subsample), full %d-step propagation "
+                                          "each, one spawned process per core" % (len(sample_idx), Nt))
         S_host = S_dev.cpu().numpy()
         acc_host = acc_full.cpu().numpy()
         l2s, worst = [], []

@@ -177,6 +177,24 @@ tdse_status tdse_check(tdse_batch* batch, int64_t* first_bad_host, void* stream)
 tdse_status tdse_energy_distribution(tdse_batch* batch, const double* E_grid_host, int32_t n_energies,
                                      double epsilon, double* P_dev, void* stream);
 
+/* Time-dependent ionisation probability of every instance's current state (Sec. 6.1, last
+ * paragraph: integrating P(E, t) over energy gives the ionisation probability, i.e. the electron
+ * density the TDSE itself predicts):
+ *     ion_i = sum_k w_k P_i(E_k),  w = trapezoid weights of the nodes: w_0 = (E_1 - E_0)/2,
+ *             w_k = (E_{k+1} - E_{k-1})/2, w_last = (E_last - E_{last-1})/2,
+ * with P_i(E_k) exactly as tdse_energy_distribution computes it at resolution epsilon.  The
+ * integral is meant over the continuum: the soft-core potential vanishes at infinity, so the nodes
+ * should start at the threshold E = 0 and reach an energy beyond which P is negligible, with a
+ * spacing well below epsilon (P varies on that scale).  At finite epsilon a bound state contributes
+ * the Lorentzian tail above the threshold, atan(epsilon / |E_b|) / pi for an eigenstate at E_b.
+ *   E_nodes_host  n_nodes >= 2 strictly ascending energies (a.u., host)
+ *   P_dev         NULL, or out: n_inst x n_nodes doubles, the distribution at the nodes
+ *   ion_dev       out: n_inst doubles, row i = instance i in creation order
+ * FP64 and MIXED batches (FP64 solves and sums).  Synchronous, with the allocations of
+ * tdse_energy_distribution plus the weights (and P when P_dev is NULL) for the call. */
+tdse_status tdse_ionisation(tdse_batch* batch, const double* E_nodes_host, int32_t n_nodes, double epsilon,
+                            double* P_dev, double* ion_dev, void* stream);
+
 /* Populations of every instance's current state (Sec. 7.5: the time-dependent ground-state
  * population and the probability of finding the electron near the nucleus):
  *     out[2 i]     = | sum_j psi0_j psi_i,j dx |^2        (ground-state population)
@@ -311,7 +329,9 @@ tdse_status tdse_autotune(tdse_batch* batch, const double* E_dev, double* d_dev,
  *                   element k of a row being sample n = sample_base + k
  *   psi_dev         in/out, caller-owned, 32*ceil(n_inst/32)*N complex doubles (re, im) in the
  *                   lane-interleaved layout: instance i, point j at complex index
- *                   ((i/32)*N + j)*32 + i%32 (the padding lanes are never read or written)
+ *                   ((i/32)*N + j)*32 + i%32.  The padding lanes of the last group (i >= n_inst)
+ *                   must be allocated and hold finite values: they are read by the sweeps but
+ *                   never written, and they never mix with the real instances' lanes
  *   other arguments as tdse_propagate; no non-finite flags are reported.
  * Sizes whose scratch does not fit the array return TDSE_ERR_ARG with the limit in the message;
  * up to that limit the grid is shrunk to what fits (fewer CTAs, so slower than tdse_propagate).

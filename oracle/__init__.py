@@ -19,6 +19,9 @@ with respect to every field sample).
 ``energy_distribution``: the time-dependent electron energy distribution P(E) of a state through the
 resolvent of the field-free Hamiltonian (Sec. 6.1).
 
+``ionisation``: the energy integral of P(E, t) over the continuum, the time-dependent ionisation
+probability (Sec. 6.1, last paragraph).
+
 ``populations``: the ground-state population and the near-core probability of a state (Sec. 7.5).
 
 ``resample_field``: the input step of Sec. 4.2, a coarsely sampled field moved to t = 0 and
@@ -169,6 +172,25 @@ def energy_distribution(psi, E_grid, dx, a, eps, Z=1.0, scheme=FULL_CN):
     _check(lib().oracle_energy_distribution(psi.size, dx, a, Z, scheme, psi.view(np.float64).ctypes.data_as(_dp),
                                             _ptr(Eg), Eg.size, eps, _ptr(P)), "oracle_energy_distribution")
     return P
+
+
+def ionisation(psi, E_nodes, dx, a, eps, Z=1.0, scheme=FULL_CN):
+    """Time-dependent ionisation probability of a state (Sec. 6.1, last paragraph: the integral of
+    P(E, t) over energy).  Reading: the integral runs over the continuum, E >= 0 (the soft-core
+    potential vanishes at infinity, so the bound states lie below 0), and is taken by the
+    trapezoidal rule on the caller's ascending nodes E_nodes (at least two; the first one is the
+    threshold, the last one an energy beyond which P is negligible):
+        Ion = sum_k w_k P(E_k),  w_0 = (E_1 - E_0)/2,  w_k = (E_{k+1} - E_{k-1})/2,  w_last = (E_last - E_{last-1})/2,
+    with P from ``energy_distribution`` at resolution eps."""
+    E = np.asarray(E_nodes, dtype=np.float64)
+    if E.size < 2 or np.any(np.diff(E) <= 0):
+        raise ValueError("need at least two strictly ascending energy nodes")
+    P = energy_distribution(psi, E, dx, a, eps, Z, scheme)
+    w = np.empty(E.size)
+    w[0] = 0.5 * (E[1] - E[0])
+    w[-1] = 0.5 * (E[-1] - E[-2])
+    w[1:-1] = 0.5 * (E[2:] - E[:-2])
+    return float(np.sum(w * P))
 
 
 def populations(psi, psi0, dx, a, r_core, Z=1.0):

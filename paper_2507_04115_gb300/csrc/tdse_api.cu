@@ -949,6 +949,49 @@ tdse_status tdse_energy_distribution(tdse_batch* b, const double* E_grid_host, i
     return TDSE_OK;
 }
 
+tdse_status tdse_ionisation(tdse_batch* b, const double* E_nodes_host, int32_t n_nodes, double epsilon,
+                            double* P_dev, double* ion_dev, void* stream)
+{
+    if (!b || !E_nodes_host || !ion_dev) return fail(TDSE_ERR_ARG, "tdse_ionisation: NULL argument");
+    if (n_nodes < 2 || n_nodes > (1 << 20)) return fail(TDSE_ERR_ARG, "tdse_ionisation: n_nodes out of [2, 2^20]");
+    for (int k = 1; k < n_nodes; ++k)
+        if (!(E_nodes_host[k] > E_nodes_host[k - 1]))
+            return fail(TDSE_ERR_ARG, "tdse_ionisation: energy nodes must be strictly ascending (node " + std::to_string(k) + ")");
+    if (!b->initialized) return fail(TDSE_ERR_STATE, "tdse_ionisation: no state");
+    // trapezoid weights of the nodes
+    std::vector<double> w(n_nodes);
+    w[0] = 0.5 * (E_nodes_host[1] - E_nodes_host[0]);
+    w[n_nodes - 1] = 0.5 * (E_nodes_host[n_nodes - 1] - E_nodes_host[n_nodes - 2]);
+    for (int k = 1; k < n_nodes - 1; ++k) w[k] = 0.5 * (E_nodes_host[k + 1] - E_nodes_host[k - 1]);
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    double* d_w = nullptr;
+    double* d_P = nullptr;
+    auto release = [&]() {
+        cudaFree(d_w);
+        if (!P_dev) cudaFree(d_P);
+    };
+    cudaError_t e = cudaMalloc(&d_w, sizeof(double) * n_nodes);
+    if (e == cudaSuccess && !P_dev) e = cudaMalloc(&d_P, sizeof(double) * (size_t)b->n_inst * n_nodes);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "tdse_ionisation: cudaMalloc");
+    }
+    double* P = P_dev ? P_dev : d_P;
+    tdse_status s = tdse_energy_distribution(b, E_nodes_host, n_nodes, epsilon, P, stream);   // synchronises
+    if (s != TDSE_OK) {
+        release();
+        return s;
+    }
+    e = cudaMemcpyAsync(d_w, w.data(), sizeof(double) * n_nodes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_ionisation(P, b->n_inst, n_nodes, d_w, ion_dev, b->sm_count, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "tdse_ionisation");
+    return TDSE_OK;
+}
+
 tdse_status tdse_populations(tdse_batch* b, double r_core, double* out_dev, void* stream)
 {
     if (!b || !out_dev) return fail(TDSE_ERR_ARG, "tdse_populations: NULL argument");

@@ -158,6 +158,10 @@ cudaError_t launch_energy_distribution(int mixed, const GroupDesc* d_groups, con
                                        int scheme, void* d_piv, const int64_t* d_piv_off, int64_t piv_elems,
                                        void* d_scratch, int n_max, int sm_count, double* P_out, cudaStream_t st);
 
+// Ionisation probability: out[i] = sum_k w[k] P[i * nE + k] (one warp per instance).
+cudaError_t launch_ionisation(const double* d_P, int64_t n_inst, int nE, const double* d_w, double* d_out,
+                              int sm_count, cudaStream_t st);
+
 // Field ingestion (tdse_field.cu): DFT coefficients of every coarse row (n_rows x (M/2 + 1) complex
 // doubles in d_coef), then the zero-padded interpolant at n_fine samples per row.
 cudaError_t launch_resample_field(const double* coarse, int64_t n_rows, int M, double dt_c, double dt_f,

@@ -176,7 +176,34 @@ __global__ void k_ed_solve(const GroupDesc* __restrict__ groups, const ClassDesc
     }
 }
 
+// Ionisation probability (Sec. 6.1, last paragraph): Ion_i = sum_k w_k P_i(E_k), the quadrature of
+// the energy distribution over the caller's nodes.  One warp per instance, lanes striding over the
+// energies, FP64 sums combined by shuffles (fixed order: deterministic).
+__global__ void k_ionisation(const double* __restrict__ P, int64_t n_inst, int nE, const double* __restrict__ w,
+                             double* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n_inst; i += n_warps) {
+        const double* row = P + i * (int64_t)nE;
+        double s = 0.0;
+        for (int k = lane; k < nE; k += kLanes) s = fma(w[k], row[k], s);
+        s = warp_sum(s);
+        if (lane == 0) out[i] = s;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_ionisation(const double* d_P, int64_t n_inst, int nE, const double* d_w, double* d_out,
+                              int sm_count, cudaStream_t st)
+{
+    if (n_inst == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n_inst + 7) / 8, (int64_t)sm_count * 8);
+    k_ionisation<<<(unsigned)blocks, 256, 0, st>>>(d_P, n_inst, nE, d_w, d_out);
+    return cudaGetLastError();
+}
 
 int64_t energy_distribution_scratch_elems(int sm_count, int n_max) { return (int64_t)sm_count * 8 * kLanes * n_max; }
 

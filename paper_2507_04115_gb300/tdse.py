@@ -22,7 +22,7 @@ _lib = None
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
            "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_model_layout",
-           "tdse_populations",
+           "tdse_populations", "tdse_ionisation",
            "tdse_last_error")
 
 
@@ -105,6 +105,7 @@ def load(path: str | None = None):
                                       ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int, _vp]
     L.tdse_energy_distribution.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp]
     L.tdse_populations.argtypes = [_vp, ctypes.c_double, _vp, _vp]
+    L.tdse_ionisation.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -272,6 +273,19 @@ class Batch:
                                                _dev_ptr(out, "P"), _stream_ptr(stream)))
         return out
 
+    def ionisation(self, E_nodes, epsilon, out=None, P_out=None, stream=None):
+        """Ionisation probability of every instance's current state: the trapezoid integral of the
+        energy distribution over the ascending nodes E_nodes (see tdse_ionisation); a float64 device
+        tensor of n_inst values.  P_out (n_inst x len(E_nodes)) optionally receives the distribution."""
+        import torch
+        En = np.ascontiguousarray(E_nodes, dtype=np.float64)
+        if out is None:
+            out = torch.empty(self.n_inst, dtype=torch.float64, device=torch.device("cuda", self.device))
+        Pp = None if P_out is None else _dev_ptr(P_out, "P_out")
+        _check(load().tdse_ionisation(self._h, En.ctypes.data_as(_dp), int(En.size), float(epsilon), Pp,
+                                      _dev_ptr(out, "out"), _stream_ptr(stream)))
+        return out
+
     def populations(self, r_core, out=None, stream=None):
         """[i, 0]: ground-state population of instance i's current state, [i, 1]: its probability
         within |x| < r_core (see tdse_populations); a float64 device tensor n_inst x 2."""
@@ -374,11 +388,26 @@ def tdse_propagate_static(inst, n_inst, dt, n_steps, row_stride, psi, E, d, a, s
                           absorber=(20.0, 0.125), stream=None):
     """Allocation-free propagation (see include/tdse.h).  inst = (N, dx, softening, charge); psi is a
     float64 device tensor holding the lane-interleaved wavefunctions, 2 * 32 * ceil(n_inst/32) * N values."""
+    import torch
     ab = None if absorber is None else ctypes.byref(tdse_absorber(float(absorber[0]), float(absorber[1])))
     ins = tdse_instance(int(inst[0]), float(inst[1]), float(inst[2]), float(inst[3]))
-    _check(load().tdse_propagate_static(ctypes.byref(ins), int(n_inst), float(dt), ab, int(n_steps), int(row_stride),
-                                        _dev_ptr(psi, "psi"), _dev_ptr(E, "E"), _dev_ptr(d, "d"), _dev_ptr(a, "a"),
-                                        int(sample_base), int(step_begin), int(step_end), _stream_ptr(stream)))
+    for name, t in (("psi", psi), ("E", E), ("d", d), ("a", a)):
+        _dev_ptr(t, name)
+        if t.device != psi.device:
+            raise ValueError("%s is on %s, psi on %s: every buffer must be on one device" % (name, t.device, psi.device))
+    need_psi = 2 * 32 * ((int(n_inst) + 31) // 32) * int(inst[0])
+    if psi.numel() < need_psi:
+        raise ValueError("psi holds %d doubles, the lane-interleaved layout needs %d" % (psi.numel(), need_psi))
+    need_row = int(n_inst) * int(row_stride)
+    for name, t in (("E", E), ("d", d), ("a", a)):
+        if t.numel() < need_row:
+            raise ValueError("%s holds %d doubles, n_inst * row_stride = %d" % (name, t.numel(), need_row))
+    # the entry point launches on the current device: make it the buffers' device
+    with torch.cuda.device(psi.device):
+        _check(load().tdse_propagate_static(ctypes.byref(ins), int(n_inst), float(dt), ab, int(n_steps),
+                                            int(row_stride), _dev_ptr(psi, "psi"), _dev_ptr(E, "E"), _dev_ptr(d, "d"),
+                                            _dev_ptr(a, "a"), int(sample_base), int(step_begin), int(step_end),
+                                            _stream_ptr(stream)))
 
 
 def tdse_probe_pipes(device=0):

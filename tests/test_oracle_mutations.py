@@ -100,6 +100,9 @@ MUTANTS = [
     (PY_SRC, "psi[np.abs(x) < r_core]", "psi[np.abs(x) <= r_core]", "populations: closed core interval"),
     (PY_SRC, "return float(np.abs(ov) ** 2), float(core)", "return float(np.real(ov) ** 2), float(core)",
      "populations: real part for the modulus"),
+    (PY_SRC, "w[0] = 0.5 * (E[1] - E[0])", "w[0] = E[1] - E[0]", "ionisation: first trapezoid weight"),
+    (PY_SRC, "w[1:-1] = 0.5 * (E[2:] - E[:-2])", "w[1:-1] = 0.5 * (E[2:] - E[1:-1])",
+     "ionisation: interior weights from one neighbour"),
 ]
 
 PIN_FILES = ["conftest.py", "test_oracle_pins.py", "test_oracle_crosscheck.py"]

@@ -439,6 +439,41 @@ def test_energy_distribution_sum_rule(oracle_mod):
     assert abs(integral / norm - 1.0) < 2e-3
 
 
+@pytest.mark.parametrize("scheme", [FULL_CN, NUMEROV])
+def test_ionisation_equals_integrated_eigen_expansion(oracle_mod, scheme):
+    """The ionisation probability (Sec. 6.1: the energy integral of P) of any state equals the
+    exact integral of its eigen-expansion, a sum of Lorentzians:
+        int_{E_a}^{E_b} P dE = sum_k |<u_k|psi>|^2 (atan((E_b - w_k)/eps) - atan((E_a - w_k)/eps)) / pi,
+    up to the trapezoidal rule's error, bounded here by (E_b - E_a) h^2 max|P''| / 12 with
+    max|P''| <= 2 ||psi||^2 / (pi eps^3).  The state is mostly the ground state (the lower node sits
+    at its Lorentzian's peak, so wrong end weights would show) plus a continuum part.  The
+    ground state alone gives atan(eps / |w_0|)/pi over [0, inf) -- not zero at finite eps: that is
+    the Lorentzian tail of a bound state above the threshold."""
+    rng = np.random.default_rng(31)
+    N, dx, a, eps = 96, 0.25, 1.19, 0.07
+    w, U = eigh(_dense_h0(oracle_mod, N, dx, a, scheme))
+    u = U / np.sqrt(dx)
+    cont = np.nonzero(w > 0.3)[0][:6]
+    psi = (0.9 * u[:, 0] + (0.1 + 0.05j) * u[:, cont] @ rng.standard_normal(cont.size)).astype(np.complex128)
+    norm = np.sum(np.abs(psi) ** 2) * dx
+    c2 = np.abs((u.T @ psi) * dx) ** 2
+    for E_a, E_b, h in ((w[0], 3.0, eps / 200), (0.0, 4.0, eps / 100)):
+        nodes = np.linspace(E_a, E_b, int(round((E_b - E_a) / h)) + 1)
+        hh = nodes[1] - nodes[0]
+        exact = np.sum(c2 * (np.arctan((E_b - w) / eps) - np.arctan((E_a - w) / eps))) / np.pi
+        bound = (E_b - E_a) * hh ** 2 / 12 * 2 * norm / (np.pi * eps ** 3)
+        ion = oracle_mod.ionisation(psi, nodes, dx, a, eps, scheme=scheme)
+        assert abs(ion - exact) <= bound, (E_a, ion, exact, bound)
+        # the end weights matter at this resolution: a plain Riemann sum is off by far more
+        P_end = oracle_mod.energy_distribution(psi, nodes[[0, -1]], dx, a, eps, scheme=scheme)
+        assert 0.5 * hh * (P_end[0] + P_end[1]) > 3 * bound or E_a == 0.0
+    # ground state over the continuum up to far above the spectrum's top
+    nodes = np.linspace(0.0, 6.0, 12001)
+    ion0 = oracle_mod.ionisation(u[:, 0].astype(np.complex128), nodes, dx, a, eps, scheme=scheme)
+    ref0 = (np.arctan(eps / abs(w[0])) - np.arctan(eps / (6.0 - w[0]))) / np.pi
+    assert abs(ion0 - ref0) < 1e-4 * ref0
+
+
 # ---------------------------------------------------------------- field ingestion (Sec. 4.2)
 
 def test_resampling_is_exact_at_coarse_samples_and_for_band_limited_fields(oracle_mod):
