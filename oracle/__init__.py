@@ -24,6 +24,10 @@ probability (Sec. 6.1, last paragraph).
 
 ``populations``: the ground-state population and the near-core probability of a state (Sec. 7.5).
 
+``dipole_spectrum`` and ``hankel_far_field``: the output side, the Fourier transform of a(t) in the
+paper's convention and the far field of a homogeneous medium by direct grid integration of
+Eq. "Hankel long homogeneous" (Sec. 3.2, Sec. 4.3).
+
 ``resample_field``: the input step of Sec. 4.2, a coarsely sampled field moved to t = 0 and
 interpolated to the propagation step by zero-padding its DFT.
 
@@ -226,6 +230,74 @@ def resample_field(coarse, dt_coarse, dt_fine, n_fine):
         tt = t[s0:s0 + 4096]
         out[s0:s0 + 4096] = np.real(np.exp(2j * np.pi * np.outer(tt, k) / T) @ coef)
     return out
+
+
+# ------------------------------------------------------------------ far field (Sec. 3.2, Sec. 4.3)
+
+MU0 = 1.25663706212e-6   # vacuum permeability (H/m, CODATA 2018)
+
+
+def dipole_spectrum(acc, dt, omegas, weight=1.0):
+    """Source term of the far-field integral (Sec. 3.2): the temporal Fourier transform of the dipole
+    acceleration in the paper's convention (Sec. 2: F^(omega) = (2 pi)^(-1/2) int F(t) exp(i omega t) dt),
+    by the rectangle rule over the samples t_n = n dt, times a weight (the gas density at the
+    instance's point, since the macroscopic source is the density times the microscopic one):
+        weight * dt / sqrt(2 pi) * sum_n a_n exp(i omega t_n)   for every omega in ``omegas``."""
+    a = np.asarray(acc, dtype=np.float64)
+    om = np.atleast_1d(np.asarray(omegas, dtype=np.float64))
+    t = np.arange(a.size) * dt
+    out = np.zeros(om.size, dtype=np.complex128)
+    for s0 in range(0, a.size, 8192):   # bounded memory for the explicit sum
+        out += np.exp(1j * np.outer(om, t[s0:s0 + 8192])) @ a[s0:s0 + 8192]
+    return weight * dt / np.sqrt(2.0 * np.pi) * out
+
+
+def trapezoid_weights(x):
+    """Weights of the trapezoidal rule on the ascending nodes x (one node: weight 1)."""
+    x = np.asarray(x, dtype=np.float64)
+    if x.size == 1:
+        return np.ones(1)
+    w = np.empty(x.size)
+    w[0] = 0.5 * (x[1] - x[0])
+    w[-1] = 0.5 * (x[-1] - x[-2])
+    w[1:-1] = 0.5 * (x[2:] - x[:-2])
+    return w
+
+
+def hankel_far_field(S, rho_src, z_src, k, z_obs, rho_obs):
+    """Far field of a homogeneous generating medium, Eq. "Hankel long homogeneous" (Sec. 3.2), by
+    direct grid integration over the source points (Sec. 4.3):
+        E(rho, z, w) = -(mu0/(4 pi)) exp(i k z) sum_i wz_i exp(-i k z'_i) exp(i k rho^2 / (2 D_i)) / D_i
+                       * sum_j wr_j rho'_j exp(i k rho'_j^2 / (2 D_i)) S[j, i, w] J0(k rho rho'_j / D_i),
+    D_i = z - z'_i, k = k(omega_w).  Readings: the integrals are the trapezoidal rule on the source
+    nodes (wr, wz: trapezoid weights of rho' and z'); a single z' plane is the thin medium (weight 1,
+    the source then being the plane's source integrated over its thickness).  S[j, i, w] is the
+    macroscopic source (density times the microscopic dJ/dt transform) at (rho'_j, z'_i, omega_w);
+    SI units (lengths in m, k in 1/m).  Returns E[w, o] at the radii rho_obs[o] of the plane z = z_obs.
+    J0 is scipy.special.j0 (library primitive)."""
+    from scipy.special import j0
+    S = np.asarray(S, dtype=np.complex128)
+    rho = np.asarray(rho_src, dtype=np.float64)
+    z = np.asarray(z_src, dtype=np.float64)
+    kk = np.atleast_1d(np.asarray(k, dtype=np.float64))
+    ro = np.atleast_1d(np.asarray(rho_obs, dtype=np.float64))
+    if S.shape != (rho.size, z.size, kk.size):
+        raise ValueError("S must be (n_rho, n_z, n_omega)")
+    if np.any(z >= z_obs):
+        raise ValueError("the observation plane must lie beyond every source plane")
+    wr = trapezoid_weights(rho)
+    wz = trapezoid_weights(z)
+    E = np.zeros((kk.size, ro.size), dtype=np.complex128)
+    for w in range(kk.size):
+        kw = kk[w]
+        acc = np.zeros(ro.size, dtype=np.complex128)
+        for i in range(z.size):
+            D = z_obs - z[i]
+            src = wr * rho * np.exp(1j * kw * rho ** 2 / (2.0 * D)) * S[:, i, w]
+            inner = j0(kw * np.outer(ro, rho) / D) @ src
+            acc += wz[i] * np.exp(-1j * kw * z[i]) * np.exp(1j * kw * ro ** 2 / (2.0 * D)) / D * inner
+        E[w] = -MU0 / (4.0 * np.pi) * np.exp(1j * kw * z_obs) * acc
+    return E
 
 
 def spectrum(acc, dt):

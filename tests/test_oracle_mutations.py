@@ -101,6 +101,21 @@ MUTANTS = [
     (PY_SRC, "return float(np.abs(ov) ** 2), float(core)", "return float(np.real(ov) ** 2), float(core)",
      "populations: real part for the modulus"),
     (PY_SRC, "w[0] = 0.5 * (E[1] - E[0])", "w[0] = E[1] - E[0]", "ionisation: first trapezoid weight"),
+    (PY_SRC, "out += np.exp(1j * np.outer(om, t[s0:s0 + 8192]))", "out += np.exp(-1j * np.outer(om, t[s0:s0 + 8192]))",
+     "dipole spectrum: sign of the Fourier exponent"),
+    (PY_SRC, "return weight * dt / np.sqrt(2.0 * np.pi) * out", "return weight * dt * out",
+     "dipole spectrum: 1/sqrt(2 pi) of the convention"),
+    (PY_SRC, "inner = j0(kw * np.outer(ro, rho) / D) @ src", "inner = j0(kw * np.outer(ro, rho) / z_obs) @ src",
+     "Hankel: J0 argument over z instead of z - z'"),
+    (PY_SRC, "src = wr * rho * np.exp(1j * kw * rho ** 2 / (2.0 * D)) * S[:, i, w]",
+     "src = wr * rho * np.exp(-1j * kw * rho ** 2 / (2.0 * D)) * S[:, i, w]", "Hankel: sign of the source Fresnel phase"),
+    (PY_SRC, "src = wr * rho * np.exp(1j * kw * rho ** 2 / (2.0 * D)) * S[:, i, w]",
+     "src = wr * np.exp(1j * kw * rho ** 2 / (2.0 * D)) * S[:, i, w]", "Hankel: rho' of the area element dropped"),
+    (PY_SRC, "acc += wz[i] * np.exp(-1j * kw * z[i])", "acc += wz[i] * np.exp(1j * kw * z[i])",
+     "Hankel: sign of the propagator phase"),
+    (PY_SRC, "np.exp(1j * kw * ro ** 2 / (2.0 * D)) / D * inner", "np.exp(1j * kw * ro ** 2 / (2.0 * D)) * inner",
+     "Hankel: 1/(z - z') dropped"),
+    (PY_SRC, "    wz = trapezoid_weights(z)\n", "    wz = np.ones(z.size)\n", "Hankel: z' weights"),
     (PY_SRC, "w[1:-1] = 0.5 * (E[2:] - E[:-2])", "w[1:-1] = 0.5 * (E[2:] - E[1:-1])",
      "ionisation: interior weights from one neighbour"),
 ]

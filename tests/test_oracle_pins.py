@@ -474,6 +474,103 @@ def test_ionisation_equals_integrated_eigen_expansion(oracle_mod, scheme):
     assert abs(ion0 - ref0) < 1e-4 * ref0
 
 
+# ---------------------------------------------------------------- far field (Sec. 3.2, Sec. 4.3)
+
+def test_dipole_spectrum_convention_and_closed_form(oracle_mod):
+    """The source transform uses the paper's convention F^(w) = (2 pi)^(-1/2) int F(t) e^{+i w t} dt.
+    (i) At the DFT bins w_k = 2 pi k / (L dt) the rectangle rule is numpy's FFT with the opposite
+    sign: dt / sqrt(2 pi) * conj(FFT(a))_k for real a.  (ii) A Gaussian-enveloped cosine
+    exp(-(t - t0)^2 / (2 s^2)) cos(W t) has the closed-form transform
+    (s/2) [exp(i (w+W) t0 - s^2 (w+W)^2 / 2) + exp(i (w-W) t0 - s^2 (w-W)^2 / 2)], which the rectangle
+    rule reaches to rounding for a well-sampled pulse decaying inside the window (t0 != 0 fixes
+    the sign of the exponent); a density weight scales the result."""
+    rng = np.random.default_rng(41)
+    L, dt = 600, 0.05
+    a = rng.standard_normal(L)
+    k = np.array([0, 1, 7, 123, 299])
+    S = oracle_mod.dipole_spectrum(a, dt, 2 * np.pi * k / (L * dt))
+    ref = dt / np.sqrt(2 * np.pi) * np.conj(np.fft.fft(a))[k]
+    assert np.max(np.abs(S - ref)) < 1e-12 * np.max(np.abs(ref))
+    s, W, t0, dt2 = 12.0, 1.3, 150.0, 0.02
+    t = np.arange(int(300.0 / dt2) + 1) * dt2
+    sig = np.exp(-((t - t0) ** 2) / (2 * s * s)) * np.cos(W * t)
+    w = np.array([0.0, 0.9, 1.25, 1.3, 1.4, 2.0])
+    ref = 0.5 * s * (np.exp(1j * (w + W) * t0 - s * s * (w + W) ** 2 / 2) + np.exp(1j * (w - W) * t0 - s * s * (w - W) ** 2 / 2))
+    got = oracle_mod.dipole_spectrum(sig, dt2, w, weight=2.5)
+    assert np.max(np.abs(got - 2.5 * ref)) < 1e-12 * s
+
+
+def _gauss_hankel(k, D, w, rho):
+    """int_0^inf exp(i k r^2 / (2 D)) exp(-r^2 / w^2) J0(k rho r / D) r dr = exp(-kap^2 / (4 al)) / (2 al),
+    al = 1/w^2 - i k / (2 D), kap = k rho / D (the Gaussian Hankel transform with a complex width)."""
+    al = 1.0 / w ** 2 - 1j * k / (2.0 * D)
+    kap = k * np.asarray(rho) / D
+    return np.exp(-kap ** 2 / (4.0 * al)) / (2.0 * al)
+
+
+def test_hankel_thin_gaussian_source_closed_form(oracle_mod):
+    """A thin Gaussian source plane (one z' node): the direct integration equals the paraxial
+    propagation of a Gaussian, -(mu0/4pi) e^{ik(z - z0)} e^{i k rho^2/(2D)}/D times the Gaussian Hankel
+    transform with complex width (closed form), to the trapezoid rule's h^2/12 error on a fine rho'
+    grid.  Fixes the J0 argument k rho rho'/D, the sign of both Fresnel phases, the rho' weight, the
+    1/D and the prefactor."""
+    lam, w, z0, z_obs = 40e-9, 20e-6, 1e-3, 0.5
+    k = np.array([2 * np.pi / lam, 2 * np.pi / (1.3 * lam)])
+    rho_src = np.linspace(0.0, 8 * w, 1601)
+    rho_obs = np.linspace(0.0, 1.2e-3, 64)
+    S = (3.0 - 1.0j) * np.exp(-rho_src ** 2 / w ** 2)[:, None, None] * np.ones((1, 1, k.size))
+    E = oracle_mod.hankel_far_field(S, rho_src, [z0], k, z_obs, rho_obs)
+    D = z_obs - z0
+    for q in range(k.size):
+        ref = (-oracle_mod.MU0 / (4 * np.pi) * np.exp(1j * k[q] * (z_obs - z0)) * np.exp(1j * k[q] * rho_obs ** 2 / (2 * D))
+               / D * (3.0 - 1.0j) * _gauss_hankel(k[q], D, w, rho_obs))
+        assert np.max(np.abs(E[q] - ref)) < 2e-5 * np.max(np.abs(ref)), q
+
+
+def test_hankel_long_phase_matched_medium_against_adaptive_quadrature(oracle_mod):
+    """A long homogeneous medium driven in phase, S(rho', z') = exp(-rho'^2/w^2) exp(i k z'): the
+    e^{-ikz'} of the propagator cancels the source phase and the field is the z' integral of the
+    thin closed form over the medium, here by adaptive quadrature (scipy.integrate.quad).  The
+    direct grid integration (trapezoid in rho' and z') must agree to its discretisation error; a
+    wrong sign of the propagator phase leaves an e^{2ikz'} that the z' grid cannot resolve."""
+    from scipy.integrate import quad
+    lam, w, Lm, z_obs = 40e-9, 20e-6, 10e-3, 0.5
+    k = 2 * np.pi / lam
+    rho_src = np.linspace(0.0, 8 * w, 1601)   # rho' trapezoid: h^2/12 / (w^2/2) = 4.2e-6 of the field
+    z_src = np.linspace(-Lm / 2, Lm / 2, 129)
+    rho_obs = np.array([0.0, 1.5e-4, 3e-4, 6e-4])
+    S = np.exp(-rho_src ** 2 / w ** 2)[:, None] * np.exp(1j * k * z_src)[None, :]
+    E = oracle_mod.hankel_far_field(S[:, :, None], rho_src, z_src, [k], z_obs, rho_obs)[0]
+    ref = np.zeros(rho_obs.size, dtype=np.complex128)
+    for o, r in enumerate(rho_obs):
+        def f(zp, part):
+            D = z_obs - zp
+            v = np.exp(1j * k * r * r / (2 * D)) / D * _gauss_hankel(k, D, w, r)
+            return v.real if part == 0 else v.imag
+        re = quad(f, -Lm / 2, Lm / 2, args=(0,), epsabs=0, epsrel=1e-12, limit=200)[0]
+        im = quad(f, -Lm / 2, Lm / 2, args=(1,), epsabs=0, epsrel=1e-12, limit=200)[0]
+        ref[o] = -oracle_mod.MU0 / (4 * np.pi) * np.exp(1j * k * z_obs) * (re + 1j * im)
+    # the rho' trapezoid's h^2/12 term does not decay with rho, so the bound is on the field's scale
+    assert np.max(np.abs(E - ref)) < 1e-5 * np.max(np.abs(ref)), (E, ref)
+
+
+def test_hankel_thin_medium_is_the_limit_of_a_thin_slab(oracle_mod):
+    """Three source planes 2 delta apart in total (trapezoid weights delta/2, delta, delta/2) carrying
+    the same in-phase source give 2 delta times the single-plane (thin-medium) result, up to the
+    O(delta / D) change of the propagator across the slab."""
+    rng = np.random.default_rng(43)
+    lam, z_obs, delta = 50e-9, 0.8, 1e-7
+    k = np.array([2 * np.pi / lam])
+    rho_src = np.linspace(0.0, 1e-4, 65)
+    rho_obs = np.linspace(0.0, 2e-3, 17)
+    prof = (rng.standard_normal(rho_src.size) + 1j * rng.standard_normal(rho_src.size)) * np.exp(-(rho_src / 4e-5) ** 2)
+    z3 = np.array([-delta, 0.0, delta])
+    S3 = prof[:, None, None] * np.exp(1j * k[0] * z3)[None, :, None]
+    E3 = oracle_mod.hankel_far_field(S3, rho_src, z3, k, z_obs, rho_obs)
+    E1 = oracle_mod.hankel_far_field(prof[:, None, None], rho_src, [0.0], k, z_obs, rho_obs)
+    assert np.max(np.abs(E3 / (2 * delta) - E1)) < 1e-6 * np.max(np.abs(E1))
+
+
 # ---------------------------------------------------------------- field ingestion (Sec. 4.2)
 
 def test_resampling_is_exact_at_coarse_samples_and_for_band_limited_fields(oracle_mod):
