@@ -54,7 +54,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["own", "reference"], default="own")
     p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large", "resolvent", "field",
-                                                "populations"],
+                                                "populations", "hankel"],
                    default="volume",
                    help="volume = the benchmark; the others measure the other workloads (one JSON line each)")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
@@ -71,6 +71,8 @@ def parse_args():
     p.add_argument("--tune-steps", type=int, default=256, help="time steps per autotuner probe")
     p.add_argument("--instances", type=int, default=8192, help="instances per GPU (smaller = profiling case)")
     p.add_argument("--nt", type=int, default=0, help="propagate only the first nt steps (0 = whole pulse)")
+    p.add_argument("--far-field", type=int, default=1,
+                   help="also time the source spectrum and the far field (Hankel) of the volume's a(t)")
     p.add_argument("--mixed-compare", type=int, default=1,
                    help="also time the MIXED path on two chunks and propagate the oracle sample in MIXED")
     return p.parse_args()
@@ -200,6 +202,52 @@ def run_oracle_pool(jobs, workers):
     ctx = mp.get_context("spawn")
     pool = ctx.Pool(processes=workers)
     return pool
+
+
+T_AU_S = 2.4188843265857e-17      # atomic unit of time (s)
+C_M_S = 299792458.0                 # speed of light (m/s)
+
+
+def far_field_stage(tdse, torch, acc_rows, offs, dt, omega0, q_max, geom, stream, n_obs=256, z_obs=0.5,
+                    rho_obs_max=5e-3, repeats=3):
+    """The output side of the path on a volume's a(t): the source spectrum at every DFT bin with
+    q <= q_max (tdse_dipole_spectrum, homogeneous density 1) and the far field of that source at
+    n_obs radii of the plane z_obs (tdse_hankel).  Each call is timed with CUDA events on the
+    launching stream (best of `repeats`); returns (timings dict, S, E)."""
+    L = int(offs[1] - offs[0])
+    k_max = int(math.floor(q_max * omega0 * L * dt / (2 * math.pi)))
+    om = 2 * math.pi * np.arange(1, k_max + 1) / (L * dt)
+    n_r, n_z = geom["n_r"], geom["n_z"]
+    rho = np.linspace(0.0, geom["w0_m"], n_r)
+    z = np.linspace(-geom["zR_m"], geom["zR_m"], n_z)
+    k = om / T_AU_S / C_M_S
+    ro = np.linspace(0.0, rho_obs_max, n_obs)
+    n = n_r * n_z
+    S = torch.empty((n, om.size), dtype=torch.complex128, device=acc_rows.device)
+    E = torch.empty((om.size, n_obs), dtype=torch.complex128, device=acc_rows.device)
+
+    def best(fn):
+        ts = []
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    t_s = best(lambda: tdse.dipole_spectrum(acc_rows, offs, dt, om, out=S, stream=stream))
+    Sv = S.view(n_r, n_z, om.size)
+    t_h = best(lambda: tdse.hankel(Sv, rho, z, k, z_obs, ro, out=E, stream=stream))
+    terms = float(om.size) * n_obs * n * 1.0
+    res = {"source_spectrum_ms": t_s, "hankel_ms": t_h, "frequencies": int(om.size), "q_max": q_max,
+           "source_points": n, "observation_radii": n_obs, "z_obs_m": z_obs, "rho_obs_max_m": rho_obs_max,
+           "hankel_terms_per_s": terms / (t_h * 1e-3),
+           "source_sample_terms_per_s": float(n) * om.size * L / (t_s * 1e-3),
+           "how": "CUDA events around each call, best of %d; a term = one (frequency, radius, source point) "
+                  "J0-weighted product" % repeats}
+    return res, S, E
 
 
 # ------------------------------------------------------------------------------------------- own arm
@@ -344,6 +392,12 @@ def own_arm(args):
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     t_spec_ms = ev0.elapsed_time(ev1)
+
+    # the output side on this volume's a(t): source spectrum and far field (Sec. 3.2, 4.3)
+    far = None
+    if world == 1 and args.far_field:
+        far, _, _ = far_field_stage(tdse, torch, acc_full.reshape(-1), np.arange(n + 1) * L, dt, omega,
+                                    1.5 * q_cut, full.extra, stream)
 
     # end to end: host (pinned) field chunks in, d and a chunks out, through the public binding
     e2e = None
@@ -490,7 +544,7 @@ def own_arm(args):
            "gpu_launches": args.steps, "nonfinite_instance": bad,
            "setup": {"softening_fit_s": t_fit, "softening": a_soft, "ground_state_ms": t_gs_ms,
                      "spectrum_ms": t_spec_ms, "spectrum_bins": k_max},
-           "spectral_error": spec_err, "mixed": mixed}
+           "spectral_error": spec_err, "mixed": mixed, "far_field": far}
     if rank == 0:
         print(json.dumps(out), flush=True)
     batch.close()
@@ -788,6 +842,36 @@ def other_workload(args):
                         "frac": flops / t / peak, "traffic": None,
                         "achieved_how": "22 FP64 flops per point of each (instance, energy) solve; the pivot "
                                         "pass per (class, energy) is amortised and not counted"})
+        return
+
+    if args.workload == "hankel":
+        # the output side at the volume batch's shape: 8192 dipole-acceleration rows of 55160
+        # samples (synthetic: odd harmonics of 800 nm with seeded amplitudes and phases under the
+        # pulse's sin^2 envelope), their source spectrum at every bin up to 1.5 q_cut, and the far
+        # field of the 64 x 128 source points at 256 radii
+        wl = inputs.volume_batch()
+        n, dt, Nt = wl.n_inst, wl.dt, int(wl.n_steps[0])
+        omega = float(wl.omega[0])
+        L = Nt + 1
+        rng = np.random.default_rng(7)
+        t = torch.arange(L, dtype=torch.float64, device=dev) * dt
+        Tp = float(wl.n_cycles[0]) * 2 * math.pi / omega
+        env = torch.sin(math.pi * t / Tp) ** 2
+        acc = torch.zeros((n, L), dtype=torch.float64, device=dev)
+        for q in range(1, 40, 2):
+            amp = torch.from_numpy(rng.uniform(0.5, 1.5, n) * 10.0 ** (-0.1 * q)).to(dev)
+            ph = torch.from_numpy(rng.uniform(0, 2 * math.pi, n)).to(dev)
+            acc += amp[:, None] * env[None, :] * torch.cos(q * omega * t[None, :] + ph[:, None])
+        q_cut = harmonic_cutoff(float(np.max(wl.E0)), omega)
+        res, _, _ = far_field_stage(tdse, torch, acc.reshape(-1), np.arange(n + 1) * L, dt, omega, 1.5 * q_cut,
+                                    wl.extra, stream, repeats=max(1, args.steps))
+        _line("far-field (Hankel) terms/s (Sec. 3.2 Eq. Hankel long homogeneous, Sec. 4.3)",
+              res["hankel_terms_per_s"], "terms/s", args,
+              "far field of the volume batch's source: 64 r x 128 z points, %d frequencies, %d radii"
+              % (res["frequencies"], res["observation_radii"]),
+              dict(res, rows=n, samples_per_row=L,
+                   a_rows="synthetic: seeded odd harmonics under the sin^2 envelope, the volume batch's shape"),
+              dtype="f64", gpu_launches=2 * max(1, args.steps))
         return
 
     if args.workload == "adjoint":

@@ -222,6 +222,44 @@ tdse_status tdse_populations(tdse_batch* batch, double r_core, double* out_dev, 
 tdse_status tdse_resample_field(const double* coarse_dev, int64_t n_rows, int32_t M, double dt_coarse, double dt_fine,
                                 int64_t n_fine, int64_t out_stride, double* out_dev, int device, void* stream);
 
+/* Macroscopic source spectrum of every dipole-acceleration row (Sec. 3.2: the far-field integral
+ * takes the temporal Fourier transform of the macroscopic source, the gas density times the
+ * microscopic dJ/dt = a(t); Sec. 2 fixes the convention F^(w) = (2 pi)^(-1/2) int F(t) e^{+i w t} dt),
+ * by the rectangle rule over the samples t_n = n dt, n = 0..L_r-1:
+ *     out[r][w] = weight_r dt / sqrt(2 pi) sum_n a_r,n exp(i omega_w n dt)
+ *   a_dev          device, rows r at [offsets[r], offsets[r+1]) (a batch's a(t) rows with sample_base 0)
+ *   omega_host     n_omega angular frequencies (same time unit as dt; |omega| <= 1e6)
+ *   weight_dev     NULL (weight 1) or device n_rows doubles: the gas density of each row's point
+ *   out_dev        device, n_rows x n_omega complex values as (re, im) double pairs, row-major
+ * FP64.  Asynchronous on the stream (stream-ordered allocation of the offsets and frequencies).
+ * The rows of a volume laid out radius-major (row = i_rho * n_z + i_z) give the source layout of
+ * tdse_hankel directly. */
+tdse_status tdse_dipole_spectrum(const double* a_dev, const int64_t* offsets_host, int64_t n_rows, double dt,
+                                 const double* omega_host, int32_t n_omega, const double* weight_dev,
+                                 double* out_dev, void* stream);
+
+/* Far field of a homogeneous generating medium, Eq. "Hankel long homogeneous" (Sec. 3.2), evaluated
+ * by direct grid integration over the source points as the paper's HANKEL module does (Sec. 4.3):
+ *     E(rho_o, z, w) = -(mu0/(4 pi)) e^{i k z} sum_i wz_i e^{-i k z'_i} e^{i k rho_o^2/(2 D_i)} / D_i
+ *                      * sum_j wr_j rho'_j e^{i k rho'_j^2/(2 D_i)} S[j][i][w] J0(k rho_o rho'_j / D_i),
+ * D_i = z - z'_i, k = k(omega_w), wr and wz the trapezoidal weights of the source radii and planes
+ * (a single plane, n_z = 1, is the thin medium with weight 1: its source is the plane's source
+ * integrated over the thickness).  SI units: lengths in m, k in 1/m, mu0 = 1.25663706212e-6 H/m;
+ * E takes the source's units times H.
+ *   S_dev          device, n_rho x n_z x n_omega complex (re, im) values, S[j][i][w] at
+ *                  ((j * n_z + i) * n_omega + w): the macroscopic source (density times the
+ *                  transformed dipole acceleration, see tdse_dipole_spectrum) at (rho'_j, z'_i, omega_w)
+ *   rho_src_host   n_rho radii, >= 0, strictly ascending (n_rho <= 2048)
+ *   z_src_host     n_z planes, strictly ascending, all below z_obs
+ *   k_host         n_omega wave numbers k(omega_w) > 0 (n_omega <= 65535)
+ *   rho_obs_host   n_obs observation radii >= 0 in the plane z = z_obs
+ *   E_dev          device, n_omega x n_obs complex (re, im) values, E[w][o]
+ * FP64 throughout (the phases k z' reach 1e6 rad).  Asynchronous on the stream on `device`
+ * (stream-ordered allocation of the grids). */
+tdse_status tdse_hankel(const double* S_dev, const double* rho_src_host, int32_t n_rho, const double* z_src_host,
+                        int32_t n_z, const double* k_host, int32_t n_omega, double z_obs, const double* rho_obs_host,
+                        int32_t n_obs, double* E_dev, int device, void* stream);
+
 /* Power spectrum of sampled signals (Sec. 3.1 / App. A: the source term enters Maxwell's
  * equations through its Fourier transform):
  *     S_i[k] = dt^2 |sum_{n=0}^{L_i - 1} a_i[n] exp(-2 pi i k n / L_i)|^2,  k = k_begin .. k_end - 1,

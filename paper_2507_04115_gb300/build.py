@@ -17,7 +17,7 @@ BUILD = os.path.join(CSRC, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libtdse.so")
 SOURCES = ["tdse_api.cu", "tdse_kernels.cu", "tdse_full_cn.cu", "tdse_numerov.cu", "tdse_static.cu", "tdse_probe.cu", "tdse_adjoint.cu",
-           "tdse_autotune.cu", "tdse_resolvent.cu", "tdse_field.cu"]
+           "tdse_autotune.cu", "tdse_resolvent.cu", "tdse_field.cu", "tdse_hankel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I" + INCLUDE, "-I" + CSRC]
 

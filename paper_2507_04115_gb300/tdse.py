@@ -22,7 +22,7 @@ _lib = None
 EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse_propagate", "tdse_get_psi",
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
            "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_model_layout",
-           "tdse_populations", "tdse_ionisation",
+           "tdse_populations", "tdse_ionisation", "tdse_dipole_spectrum", "tdse_hankel",
            "tdse_last_error")
 
 
@@ -106,6 +106,9 @@ def load(path: str | None = None):
     L.tdse_energy_distribution.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp]
     L.tdse_populations.argtypes = [_vp, ctypes.c_double, _vp, _vp]
     L.tdse_ionisation.argtypes = [_vp, _dp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]
+    L.tdse_dipole_spectrum.argtypes = [_vp, _i64p, ctypes.c_int64, ctypes.c_double, _dp, ctypes.c_int32, _vp, _vp, _vp]
+    L.tdse_hankel.argtypes = [_vp, _dp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_double,
+                              _dp, ctypes.c_int32, _vp, ctypes.c_int, _vp]
     L.tdse_last_error.argtypes = []
     L.tdse_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -354,6 +357,52 @@ def spectrum(a, offsets, dt, k_begin, k_end, out=None, stream=None):
         out = torch.empty((n_rows, k_end - k_begin), dtype=torch.float64, device=a.device)
     _check(load().tdse_spectrum(_dev_ptr(a, "a"), offs.ctypes.data_as(_i64p), n_rows, float(dt), int(k_begin),
                                 int(k_end), _dev_ptr(out, "S"), _stream_ptr(stream)))
+    return out
+
+
+def dipole_spectrum(a, offsets, dt, omegas, weight=None, out=None, stream=None):
+    """out[r, w] = weight_r dt/sqrt(2 pi) sum_n a_r,n exp(i omegas[w] n dt) (see tdse_dipole_spectrum);
+    a is a float64 device tensor holding the rows at offsets; returns a complex128 device tensor."""
+    import torch
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    om = np.ascontiguousarray(np.atleast_1d(omegas), dtype=np.float64)
+    n_rows = offs.size - 1
+    if out is None:
+        out = torch.empty((n_rows, om.size), dtype=torch.complex128, device=a.device)
+    if out.dtype != torch.complex128 or not out.is_contiguous() or out.numel() < n_rows * om.size:
+        raise ValueError("out must be a contiguous complex128 tensor of n_rows x len(omegas)")
+    wp = None
+    if weight is not None:
+        wp = _dev_ptr(weight, "weight")
+        if weight.numel() < n_rows:
+            raise ValueError("weight needs one value per row")
+    with torch.cuda.device(a.device):
+        _check(load().tdse_dipole_spectrum(_dev_ptr(a, "a"), offs.ctypes.data_as(_i64p), n_rows, float(dt),
+                                           om.ctypes.data_as(_dp), int(om.size), wp,
+                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def hankel(S, rho_src, z_src, k, z_obs, rho_obs, out=None, stream=None):
+    """Far field E[w, o] of a homogeneous medium (see tdse_hankel).  S: complex128 device tensor
+    (n_rho, n_z, n_omega); grids are host arrays (SI units); returns a complex128 device tensor
+    (n_omega, n_obs)."""
+    import torch
+    rs = np.ascontiguousarray(np.atleast_1d(rho_src), dtype=np.float64)
+    zs = np.ascontiguousarray(np.atleast_1d(z_src), dtype=np.float64)
+    kk = np.ascontiguousarray(np.atleast_1d(k), dtype=np.float64)
+    ro = np.ascontiguousarray(np.atleast_1d(rho_obs), dtype=np.float64)
+    if S.dtype != torch.complex128 or not S.is_cuda or not S.is_contiguous() or tuple(S.shape) != (rs.size, zs.size, kk.size):
+        raise ValueError("S must be a contiguous complex128 CUDA tensor of shape (n_rho, n_z, n_omega)")
+    if out is None:
+        out = torch.empty((kk.size, ro.size), dtype=torch.complex128, device=S.device)
+    if out.dtype != torch.complex128 or not out.is_contiguous() or out.numel() < kk.size * ro.size or out.device != S.device:
+        raise ValueError("out must be a contiguous complex128 tensor of n_omega x n_obs on S's device")
+    with torch.cuda.device(S.device):
+        _check(load().tdse_hankel(ctypes.c_void_p(S.data_ptr()), rs.ctypes.data_as(_dp), int(rs.size),
+                                  zs.ctypes.data_as(_dp), int(zs.size), kk.ctypes.data_as(_dp), int(kk.size),
+                                  float(z_obs), ro.ctypes.data_as(_dp), int(ro.size), ctypes.c_void_p(out.data_ptr()),
+                                  int(S.device.index or 0), _stream_ptr(stream)))
     return out
 
 

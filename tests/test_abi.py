@@ -106,3 +106,39 @@ def test_layout_cost_model_on_the_host(lib):
         tdse.model_layout([8], 0.2, 1.19, 0.05)
     with pytest.raises(tdse.TDSEError):
         tdse.model_layout([512], 0.2, 1.19, 0.05, sm_count=0)
+
+
+def test_far_field_entry_points_reject_bad_grids_without_gpu(lib):
+    """tdse_dipole_spectrum and tdse_hankel validate on the host before any CUDA call."""
+    from paper_2507_04115_gb300 import tdse
+    dp = ctypes.POINTER(ctypes.c_double)
+    fake = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+
+    def arr(v):
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        return a, a.ctypes.data_as(dp)
+
+    rho, prho = arr([0.0, 1e-5, 2e-5])
+    z, pz = arr([-1e-3, 0.0, 1e-3])
+    k, pk = arr([1e8])
+    ro, pro = arr([0.0, 1e-3])
+    good = dict(rho=prho, nr=3, z=pz, nz=3, k=pk, nk=1, zo=0.5, ro=pro, no=2)
+    bad = [dict(nr=0), dict(z=arr([0.0, -1e-3, 1e-3])[1]), dict(zo=1e-3), dict(k=arr([-1.0])[1]),
+           dict(ro=arr([0.0, -1.0])[1]), dict(rho=arr([-1e-6, 1e-5, 2e-5])[1]), dict(nr=4096)]
+    keep = [rho, z, k, ro]
+    for case in bad:
+        kw = dict(good)
+        kw.update(case)
+        rc = lib.tdse_hankel(fake, kw["rho"], kw["nr"], kw["z"], kw["nz"], kw["k"], kw["nk"], kw["zo"], kw["ro"],
+                             kw["no"], fake, 0, None)
+        assert rc == tdse.TDSE_ERR_ARG, case
+    offs = np.array([0, 10, 5], dtype=np.int64)       # decreasing
+    om, pom = arr([0.1])
+    rc = lib.tdse_dipole_spectrum(fake, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 2, 0.02, pom, 1, None,
+                                  fake, None)
+    assert rc == tdse.TDSE_ERR_ARG
+    offs = np.array([0, 10], dtype=np.int64)
+    rc = lib.tdse_dipole_spectrum(fake, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1, -0.02, pom, 1, None,
+                                  fake, None)
+    assert rc == tdse.TDSE_ERR_ARG
+    del keep

@@ -222,17 +222,20 @@ def test_volume_batch_full_size_sampled(env, launch):
     b.close()
 
 
-def _full_size_prefix(tdse, oracle, wl, precision, steps, n_sample, tol, seed):
+# MIXED prefixes are compared on the wavefunction: over the first few hundred steps the field is
+# weak and d, a are ~1e-5, so their float-rounding noise (psi rounded to 2^-24 every step, ~1e-6 of
+# <|x|> after a few hundred steps) is not a useful relative measure.  psi itself random-walks away
+# from the FP64 oracle by ~6e-8 sqrt(steps) relative per step's rounding: 1e-5 of ||psi|| bounds
+# prefixes of up to ~1000 steps with a wide margin.  The spectral bound of the MIXED path is
+# asserted on complete propagations (test_gpu_fullsize.py).
+MIXED_PSI_PREFIX = 1e-5
+
+
+def _full_size_prefix(tdse, oracle, wl, precision, steps, n_sample, seed):
     """A full-size workload batch with each instance's own Nt, laid out like the benchmark (rows of
     steps + 1 samples), propagated over its first `steps` steps with the planner's shape;
-    n_sample instances compared one by one with the oracle.
-
-    Over the first few hundred steps the field is still weak and d, a are small (|d| ~ 1e-5), so
-    the MIXED comparison uses a floor of 1e-2 on the signal scale: float psi leaves an absolute
-    error of ~1e-6 in <x> over boxes of +-600 a.u. (rounding of 2^-24 times the box's extent),
-    which the MIXED bound of 2e-3 is not stated against; what the prefix checks at full size is the
-    layout (classes, slots, rows), where a fault gives errors of order one."""
-    floor = 1e-5 if precision == 0 else 1e-2
+    n_sample instances compared one by one with the oracle: FP64 on d and a (RTOL_SERIES), MIXED
+    on psi at the end of the prefix (MIXED_PSI_PREFIX of the norm)."""
     from paper_2507_04115_gb300 import inputs
     n = wl.n_inst
     classes = sorted(set(zip(wl.N.tolist(), wl.dx.tolist())))
@@ -255,17 +258,23 @@ def _full_size_prefix(tdse, oracle, wl, precision, steps, n_sample, tol, seed):
     b.propagate(Ef, d, acc, 0, steps)
     torch.cuda.synchronize()
     assert b.check() == -1
+    sample = inputs.subsample(n, n_sample, seed)
+    psis = {int(i): b.get_psi(int(i)).cpu().numpy() for i in sample}
     b.close()
     ah = acc.view(n, steps + 1).cpu().numpy()
     dh = d.view(n, steps + 1).cpu().numpy()
     Eh = E.cpu().numpy()
-    for i in inputs.subsample(n, n_sample, seed):
+    for i in sample:
         N_, dx_ = int(wl.N[i]), float(wl.dx[i])
         psi0, _, _ = oracle.ground_state(N_, dx_, a[i], **GS_KW)
         m = oracle.mask(N_, dx_, wl.mask_width, wl.mask_exponent)
-        _, d_o, a_o = oracle.propagate(psi0, Eh[i], dx_, wl.dt, a[i], mask_values=m)
-        assert _rel(dh[i], d_o, floor) < tol, i
-        assert _rel(ah[i], a_o, floor) < tol, i
+        psi_o, d_o, a_o = oracle.propagate(psi0, Eh[i], dx_, wl.dt, a[i], mask_values=m)
+        if precision == 0:
+            assert _rel(dh[i], d_o) < RTOL_SERIES, i
+            assert _rel(ah[i], a_o) < RTOL_SERIES, i
+        else:
+            err = np.linalg.norm(psis[int(i)] - psi_o) / np.linalg.norm(psi_o)
+            assert err < MIXED_PSI_PREFIX, (i, err)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -274,15 +283,15 @@ def test_uneven_batch_full_size_prefix(env, precision):
     persistent launch, first 300 steps; six sampled instances against the oracle."""
     tdse, oracle = env
     from paper_2507_04115_gb300 import inputs
-    _full_size_prefix(tdse, oracle, inputs.uneven_batch(), precision, 300, 6, RTOL_SERIES if precision == 0 else 2e-3, 102)
+    _full_size_prefix(tdse, oracle, inputs.uneven_batch(), precision, 300, 6, 102)
 
 
 def test_large_volume_mixed_full_size_prefix(env):
     """The 131072 x 4096 large volume in MIXED precision at full size, first 200 steps; four sampled
-    instances against the FP64 oracle at the MIXED bound."""
+    instances' wavefunctions against the FP64 oracle's."""
     tdse, oracle = env
     from paper_2507_04115_gb300 import inputs
-    _full_size_prefix(tdse, oracle, inputs.large_volume(), 1, 200, 4, 2e-3, 104)
+    _full_size_prefix(tdse, oracle, inputs.large_volume(), 1, 200, 4, 104)
 
 
 def test_batch_position_invariance(env):
