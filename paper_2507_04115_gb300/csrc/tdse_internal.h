@@ -23,6 +23,7 @@ constexpr int kMaxSegments = 16;    // warps per CTA at most (512 threads)
 //   nf[3j..3j+2] = the same three factors rounded to float2 (MIXED)
 //   fx[j]  = (x_j, dV_j, m_j, 0) rounded to float4 (MIXED observables and mask)
 //   vv[j]  = V_j                                                          (energy distribution)
+//   af[j]  = ab[j] rounded to float2                                      (FP64 path's float halo rows)
 struct ClassDesc {
     int64_t tab_off;      // offset (in doubles) of the class block in the table buffer
     int32_t N;
@@ -45,6 +46,8 @@ struct GroupDesc {
     int32_t cls;          // class index
     int32_t N, P, K, m;   // grid size, warps carrying segments, halo, segment length
     int32_t I;            // instances per group (32, 16, 8, 4, 2 or 1)
+    int32_t K2;           // rows of each halo next to the segment that the FP64 path runs in double
+                          // (halo_double_rows); the outer K - K2 rows run in float
 };
 
 // Device-side tables offsets inside a class block (in doubles).
@@ -57,7 +60,8 @@ __host__ __device__ inline int64_t tab_nc(const ClassDesc& c) { return c.tab_off
 __host__ __device__ inline int64_t tab_nf(const ClassDesc& c) { return c.tab_off + 11 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_fx(const ClassDesc& c) { return c.tab_off + 14 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_vv(const ClassDesc& c) { return c.tab_off + 16 * (int64_t)c.N; }
-inline int64_t tab_doubles(int N) { return 17 * (int64_t)N; }
+__host__ __device__ inline int64_t tab_af(const ClassDesc& c) { return c.tab_off + 17 * (int64_t)c.N; }
+inline int64_t tab_doubles(int N) { return 18 * (int64_t)N; }
 
 // ---- host-side planning rules shared by the allocating and the static entry points ----
 
@@ -71,6 +75,17 @@ inline int halo_for_beta(double beta)
     if (b < 1e-3) return 8;
     const int K = (int)std::ceil(std::log(1e-18) / std::log(b));
     return std::max(K, 8);
+}
+
+// Rows of a halo that the FP64 path keeps in double, counted from the segment outwards: the outer
+// K - K2 rows run in float, and the error they leave (float rounding, ~1e-7 of the values) shrinks
+// by |gamma| <= beta per double row, so beta^K2 < 1e-11 brings it below 1e-18 like the truncation.
+inline int halo_double_rows(double beta, int K)
+{
+    if (K == 0) return 0;
+    const double b = std::fabs(beta);
+    const int K2 = b < 1e-3 ? 4 : (int)std::ceil(std::log(1e-11) / std::log(b));
+    return std::min(K, std::max(K2, 4));
 }
 
 // Segments of a class: at most the CTA's warps, and every segment at least four halos long

@@ -46,6 +46,7 @@ __global__ void k_build_tables(const ClassDesc* cls, int n_cls, double dt, doubl
         double* mk = tab + tab_mk(C);
         ab[2 * j] = h * (1.0 / (C.dx * C.dx) + V) / C.beta;
         ab[2 * j + 1] = h * x / C.beta;
+        reinterpret_cast<float2*>(tab + tab_af(C))[j] = make_float2((float)ab[2 * j], (float)ab[2 * j + 1]);
         xv[2 * j] = x;
         xv[2 * j + 1] = dV;
         double m = 1.0;

@@ -115,3 +115,75 @@ def test_numerov_substitutions_with_exact_factors():
     assert np.max(np.abs(ys - y)) < 1e-14 * np.max(np.abs(y))
     ys5 = np.concatenate([seg(w * m, min(N, (w + 1) * m), 5) for w in range(P)])
     assert np.max(np.abs(ys5 - y)) > 1e-6 * np.max(np.abs(y))
+
+
+def _halo_double_rows(beta, K):
+    # the planner's split of a halo: the rows nearest the segment in double, enough for an error of
+    # float rounding (1e-7 of the values) to shrink below 1e-18 (beta^K2 < 1e-11); the rest in float
+    return min(K, max(4, math.ceil(math.log(1e-11) / math.log(beta))))
+
+
+def _segment_solve_split(di, off, r, lo, hi, K, K2):
+    """As _segment_solve, but the outer K - K2 rows of each halo run in float32 (complex64): the
+    forward sweep from the top of the halo to K2 rows before the segment, and both sweeps over the
+    bottom halo's rows beyond K2 after the segment (the FP64 kernel's arithmetic split)."""
+    N = di.size
+    a, b = max(0, lo - K), min(N, hi + K)
+    tf, bd = max(a, lo - K2), min(b, hi + K2)
+    c32, d32 = np.complex64(0), np.complex64(0)
+    for j in range(a, tf):                                   # float forward rows
+        piv = np.complex64(di[j]) - np.complex64(off) * c32
+        c32 = np.complex64(off) / piv
+        d32 = (np.complex64(r[j]) - np.complex64(off) * d32) / piv
+    cp = np.zeros(b - a, dtype=complex)
+    dp = np.zeros(b - a, dtype=complex)
+    c64, d64 = complex(c32), complex(d32)
+    for j in range(tf, bd):                                  # double forward rows
+        piv = di[j] - off * c64
+        c64 = off / piv
+        d64 = (r[j] - off * d64) / piv
+        cp[j - a], dp[j - a] = c64, d64
+    c32, d32 = np.complex64(c64), np.complex64(d64)
+    cf = np.zeros(b - bd, dtype=np.complex64)
+    df = np.zeros(b - bd, dtype=np.complex64)
+    for j in range(bd, b):                                   # float forward rows after the segment
+        piv = np.complex64(di[j]) - np.complex64(off) * c32
+        c32 = np.complex64(off) / piv
+        d32 = (np.complex64(r[j]) - np.complex64(off) * d32) / piv
+        cf[j - bd], df[j - bd] = c32, d32
+    y32 = np.complex64(0)
+    for j in range(b - 1, bd - 1, -1):                       # float back substitution
+        y32 = df[j - bd] - cf[j - bd] * y32
+    y = np.zeros(b - a, dtype=complex)
+    yn = complex(y32)
+    for j in range(bd - 1, lo - 1, -1):                      # double back substitution
+        yn = dp[j - a] - cp[j - a] * yn
+        y[j - a] = yn
+    return y[lo - a: hi - a]
+
+
+def test_float_outer_halo_rows_stay_at_double_rounding():
+    """Running the outer K - K2 rows of every halo in float leaves the segments at double rounding
+    against the exact solve: the float error (~1e-7 of the values) enters K2 rows before the
+    segment and shrinks by beta^K2 < 1e-11; with too few double rows it shows."""
+    N, dx, dt, a = 4096, 0.15, 0.02, 1.19
+    beta = dt / (4 * dx * dx)
+    K = _halo(beta)
+    K2 = _halo_double_rows(beta, K)
+    assert (K, K2) == (28, 17)
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    P = 12
+    m = -(-N // P)
+    for Ebar in (0.0, 0.08, -0.15):
+        di, off = _system(N, dx, dt, a, Ebar)
+        ab = np.zeros((3, N), dtype=complex)
+        ab[0, 1:] = off
+        ab[1] = di
+        ab[2, :-1] = off
+        y = solve_banded((1, 1), ab, r)
+        ys = np.concatenate([_segment_solve_split(di, off, r, w * m, min(N, (w + 1) * m), K, K2) for w in range(P)])
+        assert np.max(np.abs(ys - y)) < 1e-14 * np.max(np.abs(y)), Ebar
+        # four double rows leave the float rounding at beta^4 ~ 2e-3 of ~1e-7
+        ys4 = np.concatenate([_segment_solve_split(di, off, r, w * m, min(N, (w + 1) * m), K, 4) for w in range(P)])
+        assert np.max(np.abs(ys4 - y)) > 1e-12 * np.max(np.abs(y))
