@@ -472,19 +472,20 @@ def own_arm(args):
             mp = mb.plan()
             m_tune = dict(warps_per_cta=mp["warps_per_cta"], ctas=mp["ctas"], slice_steps=mp["slice_steps"],
                           trials=len(mt))
-        n_m = min(2, n_chunks)
+        n_m = max(1, min(2, n_chunks - 1))   # chunks after the first (untimed) one
         mb.propagate(Ec[0], dc[0], ac[0], chunks[0][0], chunks[0][1], sample_base=chunks[0][0], stream=stream)
         torch.cuda.synchronize(dev)
         e0_ = torch.cuda.Event(enable_timing=True)
         e1_ = torch.cuda.Event(enable_timing=True)
         e0_.record(stream)
-        for c in range(1, 1 + n_m):
+        timed_m = [c for c in range(1, 1 + n_m) if c < n_chunks] or [0]
+        for c in timed_m:
             s0, s1 = chunks[c]
             mb.propagate(Ec[c], dc[c], ac[c], s0, s1, sample_base=s0, stream=stream)
         e1_.record(stream)
         torch.cuda.synchronize(dev)
         m_ms = e0_.elapsed_time(e1_)
-        m_val = float(n) * N * sum(chunks[c][1] - chunks[c][0] for c in range(1, 1 + n_m)) / (m_ms * 1e-3)
+        m_val = float(n) * N * sum(chunks[c][1] - chunks[c][0] for c in timed_m) / (m_ms * 1e-3)
         mixed = {"value": m_val, "unit": UNIT, "speedup_vs_fp64": m_val / value, "steps": n_m, "launch": m_tune,
                  "dtype": "psi f32, elimination recurrence and observable sums f64"}
         mb.close()
@@ -671,56 +672,12 @@ def other_workload(args):
               note="the instance spans the lanes of one CTA's warps (lane-split layout, one SM)")
         return
 
-    if args.workload in ("uneven", "large"):
-        wl = inputs.uneven_batch() if args.workload == "uneven" else inputs.large_volume()
-        n = wl.n_inst
-        classes = sorted(set(zip(wl.N.tolist(), wl.dx.tolist())))
-        soft = _fit(softcore, wl.target_energy, classes, 0)
-        a = np.array([soft[(int(N_), float(d_))] for N_, d_ in zip(wl.N, wl.dx)])
-        Nt_max = int(wl.n_steps.max())
-        S = int(args.nt) if args.nt > 0 else 2000
-        chunks = [(c * S, (c + 1) * S) for c in range(args.warmup + args.steps)]
-        offs = np.arange(n + 1, dtype=np.int64) * (S + 1)
-        b = tdse.Batch(wl.N, wl.dx, a, wl.n_steps, wl.dt, row_offsets=offs,
-                       absorber=(wl.mask_width, wl.mask_exponent), precision=prec)
-        b.ground_state()
-        Ebuf = torch.zeros(int(offs[-1]), dtype=torch.float64, device=dev)
-        d, acc = torch.zeros_like(Ebuf), torch.zeros_like(Ebuf)
-        dh = torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory()
-        Tp = wl.n_cycles * 2 * np.pi / wl.omega
-        E0t, wt, Tpt, pht = (torch.as_tensor(v, dtype=torch.float64, device=dev) for v in (wl.E0, wl.omega, Tp, wl.phi))
+    if args.workload == "uneven":
+        uneven_full(args, torch, tdse, inputs, softcore, dev)
+        return
 
-        def fill(s0):   # field chunk generated on the device (the full field of the large volume is 104 GB)
-            t = (torch.arange(s0, s0 + S + 1, dtype=torch.float64, device=dev) * wl.dt)[None, :]
-            env = torch.where(t <= Tpt[:, None], torch.sin(np.pi * t / Tpt[:, None]) ** 2, torch.zeros_like(t))
-            Ebuf.view(n, S + 1).copy_(E0t[:, None] * env * torch.cos(wt[:, None] * (t - 0.5 * Tpt[:, None]) + pht[:, None]))
-
-        tuned = None
-        if args.autotune and not (args.warps or args.ctas_per_sm or args.slice):
-            fill(0)
-            tr = b.autotune(Ebuf, d, acc, 0, min(S, args.tune_steps), sample_base=0)
-            tuned = len(tr)
-        elif args.warps or args.ctas_per_sm or args.slice:
-            b.set_launch(args.warps, args.ctas_per_sm, args.slice)
-        pts_total, t_total = 0.0, 0.0
-        for k, (s0, s1) in enumerate(chunks):
-            fill(s0)
-            t = timed(lambda: b.propagate(Ebuf, d, acc, s0, s1, sample_base=s0))
-            if args.workload == "large":
-                dh.copy_(acc, non_blocking=True)          # a(t) streamed back per chunk
-            if k >= args.warmup:
-                pts_total += float(np.sum(wl.N.astype(np.float64) * np.clip(np.minimum(wl.n_steps, s1) - s0, 0, None)))
-                t_total += t
-        torch.cuda.synchronize(dev)
-        plan = b.plan()
-        b.close()
-        _line(METRIC, pts_total / t_total, UNIT, args, wl.name,
-              dict(instances=n, chunk_steps=S, steps_covered=chunks[-1][1], Nt_max=Nt_max, classes=len(classes),
-                   precision=args.precision, ctas=plan["ctas"], warps_per_cta=plan["warps_per_cta"],
-                   slice_steps=plan["slice_steps"], autotune_trials=tuned),
-              dtype="f64" if prec == tdse.TDSE_FP64 else "f32 psi / f64 elimination",
-              total_point_steps=wl.point_steps(),
-              note="chunks of the first steps_covered steps; field chunks synthesised on the device")
+    if args.workload == "large":
+        large_stream(args, torch, tdse, inputs, softcore, dev)
         return
 
     if args.workload == "field":
@@ -907,6 +864,257 @@ def other_workload(args):
                    layout=layout),
               dtype="f64", forward_value=pts / t_fwd, adjoint_over_forward_time=t_adj / t_fwd)
         return
+
+
+# ------------------------------------------------------------------------------------------- configuration-size runs
+
+def _oracle_pool(wl, idx, soft_of_inst):
+    """The oracle's whole-pulse propagation of instances idx, started now in spawned processes (one per
+    core); returns (pool, async result, cores).  The ground state and mask are computed once per class."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cache, jobs = {}, []
+    for i in idx:
+        N, dx = int(wl.N[i]), float(wl.dx[i])
+        if (N, dx) not in cache:
+            psi0, _, _ = oracle.ground_state(N, dx, float(soft_of_inst[i]))
+            cache[(N, dx)] = (psi0, oracle.mask(N, dx, wl.mask_width, wl.mask_exponent))
+        psi0, m = cache[(N, dx)]
+        jobs.append((psi0, wl.field_rows([i])[0], dx, wl.dt, float(soft_of_inst[i]), m, int(wl.n_steps[i])))
+    cores = max(1, min(len(jobs), os.cpu_count() or 1))
+    pool = mp.get_context("spawn").Pool(processes=cores)
+    return pool, pool.map_async(_oracle_job, jobs, chunksize=1), cores
+
+
+def _fill_rows(torch, E, offs, wl, lo, hi, s0, S, dev):
+    """Field samples n = s0 .. s0 + S of instances [lo, hi) into E at offs (row i at offs[i] - offs[lo]),
+    on the device: E0 sin^2(pi t/Tp) cos(w (t - Tp/2) + phi) for t <= Tp, 0 after."""
+    cnt = hi - lo
+    t = (torch.arange(s0, s0 + S + 1, dtype=torch.float64, device=dev) * wl.dt)[None, :]
+    Tp = torch.as_tensor(wl.n_cycles[lo:hi] * 2 * np.pi / wl.omega[lo:hi], device=dev)[:, None]
+    w = torch.as_tensor(wl.omega[lo:hi], device=dev)[:, None]
+    e0 = torch.as_tensor(wl.E0[lo:hi], device=dev)[:, None]
+    ph = torch.as_tensor(wl.phi[lo:hi], device=dev)[:, None]
+    env = torch.where(t <= Tp, torch.sin(np.pi * t / Tp) ** 2, torch.zeros_like(t))
+    E.view(cnt, S + 1).copy_(e0 * env * torch.cos(w * (t - 0.5 * Tp) + ph))
+
+
+def _fill_full_rows(torch, E, offs, wl, dev, block=256):
+    """Whole-pulse rows of every instance (row i: Nt_i + 1 samples at offs[i]), by blocks of instances."""
+    n = wl.n_inst
+    for b0 in range(0, n, block):
+        b1 = min(n, b0 + block)
+        lens = torch.as_tensor(offs[b0 + 1: b1 + 1] - offs[b0: b1], device=dev)
+        idx = torch.repeat_interleave(torch.arange(b0, b1, device=dev), lens)
+        start = torch.repeat_interleave(torch.as_tensor(offs[b0: b1], device=dev), lens)
+        t = (torch.arange(int(offs[b0]), int(offs[b1]), device=dev) - start).to(torch.float64) * wl.dt
+        prm = [torch.as_tensor(v, device=dev)[idx] for v in (wl.E0, wl.omega, wl.n_cycles * 2 * np.pi / wl.omega, wl.phi)]
+        e0, w, Tp, ph = prm
+        env = torch.where(t <= Tp, torch.sin(np.pi * t / Tp) ** 2, torch.zeros_like(t))
+        E[int(offs[b0]): int(offs[b1])] = e0 * env * torch.cos(w * (t - 0.5 * Tp) + ph)
+
+
+def _sample_errors(tdse, wl, idx, rows_gpu, refs, dev):
+    """Spectral errors (relative L2 over q <= 1.5 q_cut, worst odd harmonic) of the sampled instances'
+    a(t) rows against the oracle's; the GPU spectra come from tdse_spectrum."""
+    import oracle
+    import torch
+    l2s, hs = [], []
+    for j, i in enumerate(idx):
+        a_row = rows_gpu[j]
+        L = a_row.numel()
+        S = tdse.spectrum(a_row.to(dev).contiguous(), [0, L], wl.dt, 0, L).cpu().numpy()[0]
+        S_ref = oracle.spectrum(refs[j], wl.dt)
+        omega = float(wl.omega[i])
+        l2, h = spectral_errors(S, S_ref, omega, wl.dt, L, harmonic_cutoff(float(wl.E0[i]), omega))
+        l2s.append(l2)
+        hs.append(h)
+    return {"instances": len(idx), "rel_l2_max": max(l2s), "harmonic_rel_max": max(hs)}
+
+
+def uneven_full(args, torch, tdse, inputs, softcore, dev):
+    """The uneven batch (16384 instances, N 1024..8192, up to 198575 steps) through the whole pulse
+    of every instance, FP64 then MIXED: fields resident on the device, one persistent launch per
+    chunk of steps, the chunk sequence captured once in a CUDA graph and replayed (timed); spectral
+    error of the oracle sample (64 instances, seed 102) on the run's own a(t)."""
+    wl = inputs.uneven_batch()
+    n = wl.n_inst
+    classes = sorted(set(zip(wl.N.tolist(), wl.dx.tolist())))
+    soft = _fit(softcore, wl.target_energy, classes, 0)
+    a = np.array([soft[(int(N_), float(d_))] for N_, d_ in zip(wl.N, wl.dx)])
+    nt = wl.n_steps.astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum(nt + 1)]).astype(np.int64)
+    Nt_max = int(nt.max())
+    sample = inputs.subsample(n, 64, 102) if args.cpu_baseline else np.array([], dtype=np.int64)
+    pool = res = None
+    cores = 0
+    if sample.size:
+        pool, res, cores = _oracle_pool(wl, sample, a)
+    E = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
+    _fill_full_rows(torch, E, offs, wl, dev)
+    S = int(args.nt) if args.nt > 0 else 20000
+    chunks = [(s0, min(Nt_max, s0 + S)) for s0 in range(0, Nt_max, S)]
+    pts = wl.point_steps()
+    out, rows = {}, {}
+    for pname, prec in (("fp64", tdse.TDSE_FP64), ("mixed", tdse.TDSE_MIXED)):
+        b = tdse.Batch(wl.N, wl.dx, a, nt, wl.dt, row_offsets=offs, absorber=(wl.mask_width, wl.mask_exponent),
+                       precision=prec)
+        b.ground_state()
+        d, acc = torch.zeros_like(E), torch.zeros_like(E)
+        if args.autotune:
+            b.autotune(E, d, acc, 0, args.tune_steps, sample_base=0)
+        b.propagate(E, d, acc, 0, 1)           # the launch path once outside the capture
+        b.ground_state()
+        torch.cuda.synchronize(dev)
+        st = torch.cuda.Stream(dev)
+        st.wait_stream(torch.cuda.current_stream(dev))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            for (s0, s1) in chunks:
+                b.propagate(E, d, acc, s0, s1, sample_base=0, stream=st)
+        clocks = ClockSampler(0)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.replay()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        sec = e0.elapsed_time(e1) * 1e-3
+        plan = b.plan()
+        out[pname] = {"value": pts / sec, "seconds": sec, "clocks": clk, "nonfinite_instance": b.check(),
+                      "launch": dict((k, plan[k]) for k in ("warps_per_cta", "ctas", "slice_steps", "segments", "halo"))}
+        rows[pname] = [acc[int(offs[i]): int(offs[i + 1])].clone() for i in sample]
+        b.close()
+        del g
+    if pool is not None:
+        got = res.get()
+        refs = [r[0] for r in got]
+        pool.close()
+        pool.join()
+        for pname in out:
+            out[pname]["spectral_error"] = _sample_errors(tdse, wl, sample, rows[pname], refs, dev)
+        oracle_pts = float(np.sum(wl.N[sample].astype(np.float64) * nt[sample]))
+        out["cpu_baseline"] = {"value": oracle_pts / max(r[1] for r in got), "unit": UNIT, "cores": cores,
+                               "kind": "oracle", "sample": "the 64-instance oracle sample, whole pulses"}
+    _line(METRIC, out["fp64"]["value"], UNIT, args, wl.name,
+          dict(instances=n, classes=len(classes), Nt_max=Nt_max, chunk_steps=S, chunks=len(chunks),
+               steps_covered="every step of every instance", precision="fp64 (mixed in 'mixed')",
+               graph="the chunk sequence captured once in a CUDA graph and replayed",
+               l2="fields, d and a resident: %.1f GB each" % (offs[-1] * 8 / 1e9)),
+          dtype="f64", total_point_steps=pts, solves_per_s=n / out["fp64"]["seconds"],
+          fp64=out["fp64"], mixed=dict(out["mixed"], speedup_vs_fp64=out["mixed"]["value"] / out["fp64"]["value"]),
+          gpu_launches=len(chunks) * 2, bound={"fp64": [1e-6, 1e-6], "mixed": [1e-3, 3e-2]},
+          cpu_baseline=out.get("cpu_baseline"))
+
+
+def large_stream(args, torch, tdse, inputs, softcore, dev):
+    """The large volume (131072 x 4096, MIXED, 1800 nm, 99288 steps) streamed by chunks of steps: the
+    field chunk synthesised on the device, the propagation, and the a(t) chunk copied to pinned host
+    memory on a second stream (double-buffered, overlapping the next chunk), the timed chunks captured
+    once in a CUDA graph and replayed.  The 32 instances of the oracle sample (seed 104) also run
+    the whole pulse in a batch of their own with the same launch layout: their a(t) over the timed
+    chunks must equal the large batch's bit for bit, and their spectra are compared with the oracle."""
+    wl = inputs.large_volume()
+    n, N, dt = wl.n_inst, int(wl.N[0]), wl.dt
+    Nt = int(wl.n_steps[0])
+    a_soft = softcore.fit_softening(wl.target_energy, N, float(wl.dx[0]))
+    S = int(args.nt) if args.nt > 0 else 2000
+    n_warm, n_timed = max(1, args.warmup), max(1, args.steps)
+    sample = inputs.subsample(n, 32, 104)
+    pool = res = None
+    if args.cpu_baseline:
+        pool, res, _ = _oracle_pool(wl, sample, np.full(n, a_soft))
+    offs = np.arange(n + 1, dtype=np.int64) * (S + 1)
+    b = tdse.Batch(wl.N, wl.dx, a_soft, wl.n_steps, dt, row_offsets=offs, absorber=(wl.mask_width, wl.mask_exponent),
+                   precision=tdse.TDSE_MIXED)
+    b.ground_state()
+    Ec = [torch.zeros(int(offs[-1]), dtype=torch.float64, device=dev) for _ in range(2)]
+    dc = [torch.zeros_like(Ec[0]) for _ in range(2)]
+    ac = [torch.zeros_like(Ec[0]) for _ in range(2)]
+    hb = [torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory() for _ in range(2)]
+    sample_dev = torch.as_tensor(sample, device=dev)
+    gathered = torch.zeros((n_timed, sample.size, S + 1), dtype=torch.float64, device=dev)
+    if args.autotune:
+        _fill_rows(torch, Ec[0], offs, wl, 0, n, 0, S, dev)
+        b.autotune(Ec[0], dc[0], ac[0], 0, min(S, args.tune_steps), sample_base=0)
+        b.ground_state()
+    plan = b.plan()
+    main = torch.cuda.current_stream(dev)
+    for c in range(n_warm):                     # eager warm-up chunks (the first steps of the pulse)
+        _fill_rows(torch, Ec[c % 2], offs, wl, 0, n, c * S, S, dev)
+        b.propagate(Ec[c % 2], dc[c % 2], ac[c % 2], c * S, (c + 1) * S, sample_base=c * S)
+        hb[c % 2].copy_(ac[c % 2], non_blocking=True)
+    torch.cuda.synchronize(dev)
+    st, cs = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    st.wait_stream(main)
+    g = torch.cuda.CUDAGraph()
+    copy_done = {}
+    with torch.cuda.graph(g, stream=st):
+        for k in range(n_timed):
+            c = n_warm + k
+            s0, s1 = c * S, (c + 1) * S
+            if c - 2 in copy_done:              # buffer c % 2 is free once chunk c - 2's copy is done
+                st.wait_event(copy_done[c - 2])
+            _fill_rows(torch, Ec[c % 2], offs, wl, 0, n, s0, S, dev)
+            b.propagate(Ec[c % 2], dc[c % 2], ac[c % 2], s0, s1, sample_base=s0, stream=st)
+            done = torch.cuda.Event()
+            done.record(st)
+            cs.wait_event(done)
+            with torch.cuda.stream(cs):
+                hb[c % 2].copy_(ac[c % 2], non_blocking=True)
+                gathered[k].copy_(ac[c % 2].view(n, S + 1).index_select(0, sample_dev))
+                ev = torch.cuda.Event()
+                ev.record(cs)
+            copy_done[c] = ev
+        st.wait_stream(cs)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    g.replay()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    sec = e0.elapsed_time(e1) * 1e-3
+    bad = b.check()
+    b.close()
+    timed_pts = float(n) * N * n_timed * S
+    # the oracle sample through the whole pulse with the large batch's layout (32-wide groups, same
+    # warps and slice): the same arithmetic per instance as inside the large batch
+    k_s = sample.size
+    rows = wl.field_rows(sample)
+    so = np.concatenate([[0], np.cumsum([r.size for r in rows])])
+    Es = torch.from_numpy(np.concatenate(rows)).to(dev)
+    bs = tdse.Batch(wl.N[sample], wl.dx[sample], a_soft, wl.n_steps[sample], dt, row_offsets=so,
+                    absorber=(wl.mask_width, wl.mask_exponent), precision=tdse.TDSE_MIXED, lanes_per_instance=1)
+    bs.set_launch(plan["warps_per_cta"], 1, plan["slice_steps"])
+    bs.ground_state()
+    ds, as_ = torch.zeros_like(Es), torch.zeros_like(Es)
+    bs.propagate(Es, ds, as_)
+    torch.cuda.synchronize(dev)
+    bs.close()
+    a_rows = [as_[int(so[j]): int(so[j + 1])] for j in range(k_s)]
+    same = all(torch.equal(gathered[k, j, 1:], a_rows[j][(n_warm + k) * S + 1: (n_warm + k + 1) * S + 1])
+               for k in range(n_timed) for j in range(k_s))
+    spec = None
+    if pool is not None:
+        refs = [r[0] for r in res.get()]
+        pool.close()
+        pool.join()
+        spec = _sample_errors(tdse, wl, sample, a_rows, refs, dev)
+    _line(METRIC, timed_pts / sec, UNIT, args, wl.name,
+          dict(instances=n, N=N, Nt=Nt, chunk_steps=S, warmup_chunks=n_warm, timed_chunks=n_timed,
+               timed_fraction_of_pulse=n_timed * S / Nt, precision="mixed",
+               pipeline="per chunk: field synthesised on the device, tdse_propagate, a(t) chunk copied to "
+                        "double-buffered pinned host memory on a second stream overlapping the next chunk; "
+                        "the timed chunks captured once in a CUDA graph and replayed",
+               launch=dict((k, plan[k]) for k in ("warps_per_cta", "ctas", "slice_steps", "segments", "halo"))),
+          dtype="f32 psi / f64 elimination and sums", clocks=clk, nonfinite_instance=bad,
+          total_point_steps=wl.point_steps(), d2h_bytes_per_chunk=int(offs[-1]) * 8,
+          sample_matches_large_batch_bitwise=bool(same), spectral_error=spec, bound=[1e-3, 3e-2],
+          gpu_launches=n_timed)
 
 
 def main():

@@ -286,6 +286,14 @@ double class_decay(const tdse_batch* b, const ClassDesc& C)
     return b->scheme == TDSE_NUMEROV_SPLIT ? C.rho : C.beta;
 }
 
+// Halo of a class: exact to double rounding, except on the MIXED FULL_CN path, whose float
+// wavefunctions need it only far below float rounding (kMixedHaloTol).
+int class_halo(const tdse_batch* b, const ClassDesc& C)
+{
+    const bool mixed_cn = b->precision == TDSE_MIXED && b->scheme == TDSE_FULL_CN;
+    return halo_for_beta(class_decay(b, C), mixed_cn ? kMixedHaloTol : 1e-18);
+}
+
 int model_lanes(const tdse_batch* b, const std::vector<int64_t>& class_count)
 {
     const int warps = b->warps_override > 0 ? b->warps_override : default_warps(b);
@@ -295,7 +303,7 @@ int model_lanes(const tdse_batch* b, const std::vector<int64_t>& class_count)
         double work = 0.0, longest = 0.0;
         for (size_t c = 0; c < b->classes.size(); ++c) {
             const ClassDesc& C = b->classes[c];
-            const int K = halo_for_beta(class_decay(b, C));
+            const int K = class_halo(b, C);
             const int Lc = K == 0 ? 1 : L;
             const int P = Lc == 1 ? class_segments(C.N, K, warps) : std::max(1, std::min(warps, C.N / Lc));
             const int m = group_segment_length(C.N, P, Lc);
@@ -323,7 +331,7 @@ tdse_status build_groups(tdse_batch* b)
     for (int64_t i = 0; i < n_inst; ++i) ++class_count[b->inst_class[i]];
     const int L = b->lanes_request > 0 ? b->lanes_request : model_lanes(b, class_count);
     b->class_L.assign(n_cls, 1);
-    for (int c = 0; c < n_cls; ++c) b->class_L[c] = halo_for_beta(class_decay(b, b->classes[c])) == 0 ? 1 : L;
+    for (int c = 0; c < n_cls; ++c) b->class_L[c] = class_halo(b, b->classes[c]) == 0 ? 1 : L;
 
     std::vector<int64_t> order(n_inst);
     for (int64_t i = 0; i < n_inst; ++i) order[i] = i;
@@ -426,7 +434,7 @@ tdse_status build_plan(tdse_batch* b)
     b->class_K.assign(n_cls, 0);
     for (int c = 0; c < n_cls; ++c) {
         const ClassDesc& C = b->classes[c];
-        int K = halo_for_beta(class_decay(b, C));
+        int K = class_halo(b, C);
         const int L = b->class_L[c];
         // lane-split classes use every warp (short segments are the price of filling the GPU)
         const int P = L == 1 ? class_segments(C.N, K, b->warps) : std::max(1, std::min(b->warps, C.N / L));

@@ -65,15 +65,17 @@ inline int64_t tab_doubles(int N) { return 18 * (int64_t)N; }
 
 // ---- host-side planning rules shared by the allocating and the static entry points ----
 
-// Halo length K such that beta^K < 1e-18: the truncated sweeps then agree with the exact Thomas
-// solve below double rounding (|gamma| <= |beta| per point, see tdse_full_cn.cu); 0 when beta is
-// too close to 1 for truncation to pay off.
-inline int halo_for_beta(double beta)
+// Halo length K such that beta^K < tol (1e-18 by default): the truncated sweeps then agree with the
+// exact Thomas solve below double rounding (|gamma| <= |beta| per point, see tdse_full_cn.cu); 0 when
+// beta is too close to 1 for truncation to pay off.  The MIXED FULL_CN path, whose wavefunctions
+// are rounded to float every step, takes tol = kMixedHaloTol.
+constexpr double kMixedHaloTol = 1e-13;
+inline int halo_for_beta(double beta, double tol = 1e-18)
 {
     const double b = std::fabs(beta);
     if (b >= 0.85) return 0;
     if (b < 1e-3) return 8;
-    const int K = (int)std::ceil(std::log(1e-18) / std::log(b));
+    const int K = (int)std::ceil(std::log(tol) / std::log(b));
     return std::max(K, 8);
 }
 

@@ -157,3 +157,41 @@ def test_adjoint_batch_full_length_gradient(env):
     for j, i in enumerate(sample):
         err = float(np.max(np.abs(gEh[i] - refs[j])) / np.max(np.abs(refs[j])))
         assert err < 1e-9, (int(i), err)
+
+
+def test_uneven_batch_full_length_spectra(env):
+    """The uneven batch's configuration (N 1024..8192, two dx, 4-16 cycles at 800/1030/1800 nm,
+    up to 198575 steps): six instances of its oracle sample (seed 102), whole pulses, FP64 and MIXED,
+    both spectral numbers within each precision's stated bound."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    wl = inputs.uneven_batch()
+    idx = inputs.subsample(wl.n_inst, 64, 102)[:6]
+    soft_of = {}
+    for i in idx:
+        c = (int(wl.N[i]), float(wl.dx[i]))
+        if c not in soft_of:
+            soft_of[c] = oracle.fit_softening(wl.target_energy, c[0], c[1])
+    soft = np.array([soft_of[(int(wl.N[i]), float(wl.dx[i]))] for i in idx])
+    rows = wl.field_rows(idx)
+    refs = _oracle_refs(oracle, wl, idx, soft, rows)
+    for precision, bound in ((tdse.TDSE_FP64, FP64_BOUND), (tdse.TDSE_MIXED, MIXED_BOUND)):
+        offs, acc = _gpu_run(tdse, wl, idx, soft, precision, 12, rows)
+        got = _spectral_check(tdse, oracle, wl, idx, refs, acc, offs, bound)
+        print("uneven full length, precision %d: rel L2 %.3g, worst odd harmonic %.3g" % (precision, *got))
+
+
+def test_large_volume_full_length_mixed_spectra(env):
+    """The large volume's configuration in MIXED (1800 nm, 8 cycles, 99288 steps, N = 4096): four
+    instances of its oracle sample (seed 104), whole pulse, within the MIXED bound."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    wl = inputs.large_volume()
+    idx = inputs.subsample(wl.n_inst, 32, 104)[:4]
+    a = oracle.fit_softening(wl.target_energy, int(wl.N[0]), float(wl.dx[0]))
+    soft = np.full(idx.size, a)
+    rows = wl.field_rows(idx)
+    refs = _oracle_refs(oracle, wl, idx, soft, rows)
+    offs, acc = _gpu_run(tdse, wl, idx, soft, tdse.TDSE_MIXED, 12, rows)
+    got = _spectral_check(tdse, oracle, wl, idx, refs, acc, offs, MIXED_BOUND)
+    print("large volume full length, MIXED: rel L2 %.3g, worst odd harmonic %.3g" % got)
