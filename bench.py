@@ -54,7 +54,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["own", "reference"], default="own")
     p.add_argument("--workload", choices=["volume", "single", "uneven", "adjoint", "large", "resolvent", "field",
-                                                "populations", "hankel"],
+                                                "populations", "hankel", "numerov"],
                    default="volume",
                    help="volume = the benchmark; the others measure the other workloads (one JSON line each)")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
@@ -71,6 +71,9 @@ def parse_args():
     p.add_argument("--tune-steps", type=int, default=256, help="time steps per autotuner probe")
     p.add_argument("--instances", type=int, default=8192, help="instances per GPU (smaller = profiling case)")
     p.add_argument("--nt", type=int, default=0, help="propagate only the first nt steps (0 = whole pulse)")
+    p.add_argument("--secondary", type=int, default=1,
+                   help="also measure the other configurations (single atom, NUMEROV, adjoint, field ingestion) and "
+                        "the analysis of the final states, as extra keys of the line")
     p.add_argument("--far-field", type=int, default=1,
                    help="also time the source spectrum and the far field (Hankel) of the volume's a(t)")
     p.add_argument("--mixed-compare", type=int, default=1,
@@ -393,6 +396,31 @@ def own_arm(args):
     torch.cuda.synchronize(dev)
     t_spec_ms = ev0.elapsed_time(ev1)
 
+    # analysis of the final states (Sec. 6.1, 7.5): energy distribution, ionisation probability and
+    # populations of every instance after the whole pulse, on the benchmark batch itself
+    analysis = None
+    if world == 1 and args.secondary:
+        clk_a = ClockSampler(local_rank)
+        clk_a.start()
+        E_grid = np.linspace(-0.7, 2.5, 128)
+        P = torch.empty((n, E_grid.size), dtype=torch.float64, device=dev)
+        t_ed = _timed(torch, dev, stream, lambda: batch.energy_distribution(E_grid, 0.02, out=P, stream=stream))
+        nodes = np.linspace(0.0, 2.5, 401)
+        ion = torch.empty(n, dtype=torch.float64, device=dev)
+        t_ion = _timed(torch, dev, stream, lambda: batch.ionisation(nodes, 0.02, out=ion, stream=stream))
+        pops = torch.empty((n, 2), dtype=torch.float64, device=dev)
+        batch.populations(2.0, out=pops, stream=stream)
+        t_pop = _timed(torch, dev, stream, lambda: batch.populations(2.0, out=pops, stream=stream))
+        ion_h, pop_h = ion.cpu().numpy(), pops.cpu().numpy()
+        analysis = {"energy_distribution": {"solves_per_s": n * E_grid.size / t_ed, "seconds": t_ed,
+                                            "energies": int(E_grid.size), "eps": 0.02},
+                    "ionisation": {"solves_per_s": n * nodes.size / t_ion, "seconds": t_ion, "nodes": int(nodes.size),
+                                   "range_au": [0.0, 2.5], "eps": 0.02, "min": float(ion_h.min()),
+                                   "max": float(ion_h.max())},
+                    "populations": {"states_per_s": n / t_pop, "seconds": t_pop, "r_core": 2.0,
+                                    "ground_population_range": [float(pop_h[:, 0].min()), float(pop_h[:, 0].max())]},
+                    "state": "every instance after the whole %d-step pulse" % Nt, "clocks": clk_a.stop()}
+
     # the output side on this volume's a(t): source spectrum and far field (Sec. 3.2, 4.3)
     far = None
     if world == 1 and args.far_field:
@@ -508,6 +536,21 @@ def own_arm(args):
                 worst.append(wv)
             mixed["spectral_error"] = {"instances": k, "rel_l2_max": max(l2s), "harmonic_rel_max": max(worst)}
 
+    # the other configurations and rows, bounded so that the whole line stays within a few minutes
+    secondary = None
+    if world == 1 and args.secondary:
+        secondary = {}
+        for name, fn in (("single_atom", lambda: measure_single(torch, tdse, inputs, softcore, dev, stream, 1, 1, 2)),
+                         ("numerov_volume", lambda: measure_numerov(torch, tdse, inputs, softcore, dev, stream, 300, 1)),
+                         ("adjoint_batch", lambda: measure_adjoint(torch, tdse, inputs, softcore, dev, stream, 0, 1, 128)),
+                         ("field_ingestion", lambda: measure_field(torch, tdse, inputs, dev, stream))):
+            ck = ClockSampler(local_rank)
+            ck.start()
+            r = fn()
+            r["clocks"] = ck.stop()
+            secondary[name] = r
+        secondary["analysis_of_final_states"] = analysis
+
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     pts_per_launch = float(n) * N * (timed_steps / args.steps)
     # FP64 work per point-step: the whole step in FP64; in MIXED only the pivot recurrence of the
@@ -545,7 +588,7 @@ def own_arm(args):
            "gpu_launches": args.steps, "nonfinite_instance": bad,
            "setup": {"softening_fit_s": t_fit, "softening": a_soft, "ground_state_ms": t_gs_ms,
                      "spectrum_ms": t_spec_ms, "spectrum_bins": k_max},
-           "spectral_error": spec_err, "mixed": mixed, "far_field": far}
+           "spectral_error": spec_err, "mixed": mixed, "far_field": far, "secondary": secondary}
     if rank == 0:
         print(json.dumps(out), flush=True)
     batch.close()
@@ -644,32 +687,17 @@ def other_workload(args):
         return e0.elapsed_time(e1) * 1e-3
 
     if args.workload == "single":
-        wl = inputs.single_atom()
-        N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
-        a = softcore.fit_softening(wl.target_energy, N, dx)
-        E = torch.from_numpy(wl.field_rows()[0]).to(dev)
-        Nt = E.numel() - 1
-        res, shapes = {}, {}
-        for pname, pv in (("fp64", tdse.TDSE_FP64), ("mixed", tdse.TDSE_MIXED)):
-            b = tdse.Batch([N], dx, a, [Nt], dt, absorber=(wl.mask_width, wl.mask_exponent), precision=pv)
-            d, acc = torch.zeros_like(E), torch.zeros_like(E)
-            b.ground_state()
-            if args.autotune:
-                b.autotune(E, d, acc, 0, min(Nt, 512))
-            shapes[pname] = dict((k, b.plan()[k]) for k in ("lanes_per_instance", "warps_per_cta", "segments", "halo"))
-            ts = []
-            for k in range(args.warmup + args.steps):
-                b.ground_state()
-                t = timed(lambda: b.propagate(E, d, acc))
-                if k >= args.warmup:
-                    ts.append(t)
-            res[pname] = float(N) * Nt / statistics.mean(ts)
-            b.close()
-        _line(METRIC, res["fp64"], UNIT, args, "single atom N=2000 dx=0.2 dt=0.05, 800 nm 4-cycle sin^2, 8818 steps",
-              dict(N=N, dx=dx, dt=dt, Nt=Nt, step="one whole propagation of the single instance", layout=shapes),
-              dtype="f64", mixed={"value": res["mixed"], "speedup_vs_fp64": res["mixed"] / res["fp64"]},
-              solves_per_s=res["fp64"] / (N * Nt),
+        r = measure_single(torch, tdse, inputs, softcore, dev, stream, args.autotune, args.warmup, args.steps)
+        _line(METRIC, r["fp64"], UNIT, args, r["workload"], r["config"], dtype="f64",
+              mixed={"value": r["mixed"], "speedup_vs_fp64": r["mixed"] / r["fp64"]},
+              solves_per_s=r["fp64"] / r["points_per_solve"],
               note="the instance spans the lanes of one CTA's warps (lane-split layout, one SM)")
+        return
+
+    if args.workload == "numerov":
+        r = measure_numerov(torch, tdse, inputs, softcore, dev, stream, args.nt or 300, args.autotune)
+        _line(METRIC, r["fp64"]["value"], UNIT, args, r["workload"], r["config"], dtype="f64", mixed=r["mixed"],
+              fp64=r["fp64"])
         return
 
     if args.workload == "uneven":
@@ -832,38 +860,134 @@ def other_workload(args):
         return
 
     if args.workload == "adjoint":
-        wl = inputs.adjoint_batch()
-        n = wl.n_inst
-        N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
-        Nt = int(wl.n_steps[0]) if args.nt <= 0 else args.nt
-        a = softcore.fit_softening(wl.target_energy, N, dx)
-        E = torch.empty((n, Nt + 1), dtype=torch.float64, device=dev)
-        inputs.sin2_pulse_batch(Nt, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
-        E = E.reshape(-1).contiguous()
-        b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent))
+        r = measure_adjoint(torch, tdse, inputs, softcore, dev, stream, args.nt, args.autotune, args.tune_steps)
+        _line("1D-TDSE adjoint gradient, forward-equivalent grid-point-steps/s", r["value"], UNIT, args, r["workload"],
+              r["config"], dtype="f64", forward_value=r["forward_value"],
+              adjoint_over_forward_time=r["adjoint_over_forward_time"])
+        return
+
+
+def _timed(torch, dev, stream, fn):
+    """Seconds of fn's GPU work: CUDA events on the launching stream, synchronised on both sides."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def measure_single(torch, tdse, inputs, softcore, dev, stream, autotune=1, warmup=1, steps=3):
+    """The single atom (N = 2000, 8818 steps): whole propagations in FP64 and MIXED (best layout)."""
+    wl = inputs.single_atom()
+    N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+    a = softcore.fit_softening(wl.target_energy, N, dx)
+    E = torch.from_numpy(wl.field_rows()[0]).to(dev)
+    Nt = E.numel() - 1
+    res, shapes = {}, {}
+    for pname, pv in (("fp64", tdse.TDSE_FP64), ("mixed", tdse.TDSE_MIXED)):
+        b = tdse.Batch([N], dx, a, [Nt], dt, absorber=(wl.mask_width, wl.mask_exponent), precision=pv)
+        d, acc = torch.zeros_like(E), torch.zeros_like(E)
+        b.ground_state()
+        if autotune:
+            b.autotune(E, d, acc, 0, min(Nt, 512))
+        shapes[pname] = dict((k, b.plan()[k]) for k in ("lanes_per_instance", "warps_per_cta", "segments", "halo"))
+        ts = []
+        for k in range(warmup + steps):
+            b.ground_state()
+            t = _timed(torch, dev, stream, lambda: b.propagate(E, d, acc))
+            if k >= warmup:
+                ts.append(t)
+        res[pname] = float(N) * Nt / statistics.mean(ts)
+        b.close()
+    return {"fp64": res["fp64"], "mixed": res["mixed"], "points_per_solve": N * Nt,
+            "workload": "single atom N=2000 dx=0.2 dt=0.05, 800 nm 4-cycle sin^2, 8818 steps",
+            "config": dict(N=N, dx=dx, dt=dt, Nt=Nt, step="one whole propagation of the single instance", layout=shapes)}
+
+
+def measure_numerov(torch, tdse, inputs, softcore, dev, stream, steps=300, autotune=1):
+    """The paper's scheme (NUMEROV_SPLIT, Sec. 4.2) on the volume batch's shape: 8192 x 4096 over the
+    first `steps` steps, FP64 and MIXED, the soft-core a fitted on the Numerov H0."""
+    wl = inputs.volume_batch()
+    n, N, dx, dt = wl.n_inst, int(wl.N[0]), float(wl.dx[0]), wl.dt
+    a = softcore.fit_softening(wl.target_energy, N, dx, scheme=tdse.TDSE_NUMEROV_SPLIT)
+    E = torch.empty((n, steps + 1), dtype=torch.float64, device=dev)
+    inputs.sin2_pulse_batch(steps, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
+    E = E.reshape(-1).contiguous()
+    out = {}
+    for pname, pv in (("fp64", tdse.TDSE_FP64), ("mixed", tdse.TDSE_MIXED)):
+        b = tdse.Batch([N] * n, dx, a, [steps] * n, dt, absorber=(wl.mask_width, wl.mask_exponent), precision=pv,
+                       scheme=tdse.TDSE_NUMEROV_SPLIT)
         b.ground_state()
         d, acc = torch.zeros_like(E), torch.zeros_like(E)
-        if args.autotune:
-            b.autotune(E, d, acc, 0, min(Nt, args.tune_steps))
-        psi0 = b.save_state()
-        t_fwd = timed(lambda: b.propagate(E, d, acc))
-        b.load_state(psi0)
-        # loss = harmonic yield of q in [21, 31]: dL/da from the spectrum of every row
-        L = Nt + 1
-        q = np.fft.fftfreq(L, dt) * 2 * np.pi / float(wl.omega[0])
-        win = torch.from_numpy(((np.abs(q) >= 21) & (np.abs(q) <= 31)).astype(np.float64)).to(dev)
-        A = torch.fft.fft(acc.view(n, L), dim=1)
-        ga = (2 * dt * dt * torch.fft.ifft(A * win[None, :], dim=1).real * L).reshape(-1).contiguous()
-        gd = torch.zeros_like(E)
-        t_adj = timed(lambda: b.adjoint(E, gd, ga, ckpt_every=256))
-        pts = float(n) * N * Nt
-        layout = dict((k, b.plan()[k]) for k in ("lanes_per_instance", "warps_per_cta", "segments", "halo", "ctas"))
+        if autotune:
+            b.autotune(E, d, acc, 0, min(steps, 64))
+        b.ground_state()
+        t = _timed(torch, dev, stream, lambda: b.propagate(E, d, acc))
+        plan = b.plan()
+        out[pname] = {"value": float(n) * N * steps / t, "seconds": t, "nonfinite_instance": b.check(),
+                      "launch": dict((k, plan[k]) for k in ("warps_per_cta", "ctas", "slice_steps", "segments", "halo"))}
         b.close()
-        _line("1D-TDSE adjoint gradient, forward-equivalent grid-point-steps/s", pts / t_adj, UNIT, args, wl.name,
-              dict(instances=n, N=N, Nt=Nt, ckpt_every=256, loss="sum of dt^2|DFT(a)|^2 over harmonics 21-31",
-                   layout=layout),
-              dtype="f64", forward_value=pts / t_fwd, adjoint_over_forward_time=t_adj / t_fwd)
-        return
+    out["mixed"]["speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["workload"] = "NUMEROV_SPLIT (Sec. 4.2) on the volume batch: 8192 x 4096, first %d steps" % steps
+    out["config"] = dict(instances=n, N=N, dx=dx, dt=dt, steps=steps, scheme="numerov_split")
+    return out
+
+
+def measure_adjoint(torch, tdse, inputs, softcore, dev, stream, nt=0, autotune=1, tune_steps=256):
+    """The adjoint batch (1024 x 2048, 6 cycles): forward propagation and the adjoint gradient of the
+    harmonic 21-31 yield (checkpoints every 256 steps), each timed once."""
+    wl = inputs.adjoint_batch()
+    n = wl.n_inst
+    N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
+    Nt = int(wl.n_steps[0]) if nt <= 0 else nt
+    a = softcore.fit_softening(wl.target_energy, N, dx)
+    E = torch.empty((n, Nt + 1), dtype=torch.float64, device=dev)
+    inputs.sin2_pulse_batch(Nt, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
+    E = E.reshape(-1).contiguous()
+    b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent))
+    b.ground_state()
+    d, acc = torch.zeros_like(E), torch.zeros_like(E)
+    if autotune:
+        b.autotune(E, d, acc, 0, min(Nt, tune_steps))
+    psi0 = b.save_state()
+    t_fwd = _timed(torch, dev, stream, lambda: b.propagate(E, d, acc))
+    b.load_state(psi0)
+    # loss = harmonic yield of q in [21, 31]: dL/da from the spectrum of every row
+    L = Nt + 1
+    q = np.fft.fftfreq(L, dt) * 2 * np.pi / float(wl.omega[0])
+    win = torch.from_numpy(((np.abs(q) >= 21) & (np.abs(q) <= 31)).astype(np.float64)).to(dev)
+    A = torch.fft.fft(acc.view(n, L), dim=1)
+    ga = (2 * dt * dt * torch.fft.ifft(A * win[None, :], dim=1).real * L).reshape(-1).contiguous()
+    gd = torch.zeros_like(E)
+    t_adj = _timed(torch, dev, stream, lambda: b.adjoint(E, gd, ga, ckpt_every=256))
+    pts = float(n) * N * Nt
+    layout = dict((k, b.plan()[k]) for k in ("lanes_per_instance", "warps_per_cta", "segments", "halo", "ctas"))
+    b.close()
+    return {"value": pts / t_adj, "forward_value": pts / t_fwd, "adjoint_over_forward_time": t_adj / t_fwd,
+            "forward_s": t_fwd, "adjoint_s": t_adj, "workload": wl.name,
+            "config": dict(instances=n, N=N, Nt=Nt, ckpt_every=256, loss="sum of dt^2|DFT(a)|^2 over harmonics 21-31",
+                           layout=layout)}
+
+
+def measure_field(torch, tdse, inputs, dev, stream, rows=2048, repeats=2):
+    """Field ingestion (Sec. 4.2) of the volume batch's rows: 2400 coarse samples at 0.5 a.u. ->
+    55160 samples at dt = 0.02 (best of `repeats`)."""
+    wl = inputs.volume_batch()
+    n = min(rows, wl.n_inst)
+    M, dt_c, dt_f = 2400, 0.5, wl.dt
+    n_fine = int(wl.n_steps[0]) + 1
+    coarse = torch.empty((n, M - 1), dtype=torch.float64, device=dev)
+    inputs.sin2_pulse_batch(M - 2, dt_c, wl.E0[:n], float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi[:n],
+                            out=coarse, xp=torch)
+    coarse = torch.cat([coarse, torch.zeros((n, 1), dtype=torch.float64, device=dev)], dim=1).contiguous()
+    out = torch.empty((n, n_fine), dtype=torch.float64, device=dev)
+    tdse.resample_field(coarse, dt_c, dt_f, n_fine, out=out)
+    t = min(_timed(torch, dev, stream, lambda: tdse.resample_field(coarse, dt_c, dt_f, n_fine, out=out))
+            for _ in range(repeats))
+    return {"value": float(n) * n_fine / t, "unit": "fine samples/s", "seconds_per_call": t, "rows": n, "M": M,
+            "n_fine": n_fine, "fp64_instructions_per_sample": 6 * (M // 2 + 1)}
 
 
 # ------------------------------------------------------------------------------------------- configuration-size runs

@@ -182,6 +182,23 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, 
     }
 }
 
+// One forward row of the elimination in float (the MIXED path's halo rows): gamma = (cr, ci),
+// D = (Dr, Di), t = (S0_j, Xh_j)/beta rounded to float, p = psi_j.
+__device__ __forceinline__ void fwd_row_f32(float2 t, float2 p, float Eb, float inv_beta, float& cr, float& ci,
+                                            float& Dr, float& Di)
+{
+    float inv;
+    const float Qr = ci + inv_beta;
+    const float Qi = fmaf(t.y, Eb, t.x) - cr;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(fmaf(Qr, Qr, Qi * Qi)));
+    cr = Qi * inv;
+    ci = Qr * inv;
+    const float ur = p.x - Di, ui = p.y + Dr;
+    const float nDr = fmaf(cr, ui, ci * ur);
+    Di = fmaf(ci, ui, -cr * ur);
+    Dr = nDr;
+}
+
 template <bool kMixed>
 __global__ void __launch_bounds__(512, 1)
 k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const ClassDesc* __restrict__ cls,
@@ -295,10 +312,86 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
             // q_j = 1 + i s_j + beta^2 g_{j-1} the Thomas pivot, gamma = i beta g = i conj(Q)/|Q|^2,
             // D = beta d = -i gamma u with u = psi + i D_{j-1}.  Tables hold s_j/beta split as
             // (S0_j, Xh_j)/beta; Re Q = 1/beta + Im gamma_{j-1}, Im Q = s_j/beta - Re gamma_{j-1}.
-            // The recurrence for Q and gamma always runs in double.
-            double cr = 0.0, ci = 0.0;
-            R Dr = 0, Di = 0;
-            {
+            // FP64: every row in double.  MIXED: the own segment keeps the recurrence for Q and gamma
+            // in double (its stability over 1e5 steps needs it); the halo rows only converge the
+            // truncated recurrences to this path's float accuracy (the halo is kMixedHaloTol long),
+            // so they run in float, and the top halo's rows are not stored (the back substitution
+            // stops at s).
+            if constexpr (kMixed) {
+                float crf = 0.0f, cif = 0.0f;
+                R Dr = 0, Di = 0;
+                const float inv_beta_f = d2f(inv_beta);
+                const float Ebf = d2f(Eb);
+                const float2* __restrict__ taf = reinterpret_cast<const float2*>(tab + tab_af(C));
+                {
+                    const Cx* pj = ps + (int64_t)lo * kLanes + lane;
+                    Cx pa = lo < s ? ld_cg(pj) : mk(R(0), R(0));
+                    Cx pb = lo + 1 < s ? ld_cg(pj + kLanes) : mk(R(0), R(0));
+                    const Cx* pnext = pj + 2 * kLanes;
+                    for (int j = lo; j < s; ++j) {
+                        const Cx p = pa;
+                        pa = pb;
+                        if (j + 2 < s) pb = ld_cg(pnext);
+                        pnext += kLanes;
+                        fwd_row_f32(__ldg(taf + j), p, Ebf, inv_beta_f, crf, cif, Dr, Di);
+                    }
+                }
+                double cr = crf, ci = cif;
+                Cx* r = sc + (int64_t)(s - lo) * (2 * kLanes);
+                {
+                    // pointers advance by increments: no 64-bit index arithmetic inside the loop
+                    const Cx* pj = ps + (int64_t)s * kLanes + lane;
+                    Cx pa = s < e ? ld_cg(pj) : mk(R(0), R(0));
+                    Cx pb = s + 1 < e ? ld_cg(pj + kLanes) : mk(R(0), R(0));
+                    const Cx* pnext = pj + 2 * kLanes;
+                    const double2* tp = tab_ab2 + s;
+#pragma unroll 2
+                    for (int j = s; j < e; ++j) {
+                        const Cx p = pa;
+                        pa = pb;
+                        if (j + 2 < e) pb = ld_cg(pnext);
+                        pnext += kLanes;
+                        const double2 t = __ldg(tp);
+                        ++tp;
+                        const double Qr = F.add(ci, inv_beta);
+                        const double Qi = F.sub(fma(t.y, Eb, t.x), cr);
+                        // gamma is rounded to float right after, so a 2^-40 reciprocal suffices (the
+                        // recurrence damps an error by beta^2 per point; it stays ~1e-12)
+                        const double inv = rcp_pos_2nd(fma(Qr, Qr, F.mul(Qi, Qi)));
+                        cr = F.mul(Qi, inv);
+                        ci = F.mul(Qr, inv);
+                        const R gr = d2f(cr);
+                        const R gi = d2f(ci);
+                        const R ur = F.sub(p.x, Di);
+                        const R ui = F.add(p.y, Dr);
+                        Dr = fma(gr, ui, F.mul(gi, ur));
+                        Di = fma(gi, ui, F.mul(-gr, ur));
+                        r[lane] = mk(gr, gi);
+                        r[kLanes + lane] = mk(Dr, Di);
+                        r += 2 * kLanes;
+                    }
+                }
+                if (e < hi) {
+                    crf = d2f(cr);
+                    cif = d2f(ci);
+                    const Cx* pj = ps + (int64_t)e * kLanes + lane;
+                    Cx pa = ld_cg(pj);
+                    Cx pb = e + 1 < hi ? ld_cg(pj + kLanes) : mk(R(0), R(0));
+                    const Cx* pnext = pj + 2 * kLanes;
+                    for (int j = e; j < hi; ++j) {
+                        const Cx p = pa;
+                        pa = pb;
+                        if (j + 2 < hi) pb = ld_cg(pnext);
+                        pnext += kLanes;
+                        fwd_row_f32(__ldg(taf + j), p, Ebf, inv_beta_f, crf, cif, Dr, Di);
+                        r[lane] = mk(crf, cif);
+                        r[kLanes + lane] = mk(Dr, Di);
+                        r += 2 * kLanes;
+                    }
+                }
+            } else {
+                double cr = 0.0, ci = 0.0;
+                R Dr = 0, Di = 0;
                 // pointers advance by increments: no 64-bit index arithmetic inside the loop
                 const Cx* pj = ps + (int64_t)lo * kLanes + lane;
                 Cx pa = lo < hi ? ld_cg(pj) : mk(R(0), R(0));
@@ -316,25 +409,14 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     ++tp;
                     const double Qr = F.add(ci, inv_beta);
                     const double Qi = F.sub(fma(t.y, Eb, t.x), cr);
-                    // MIXED: gamma is rounded to float right after, so a 2^-40 reciprocal suffices
-                    // (the recurrence damps an error by beta^2 per point; it stays ~1e-12)
-                    const double q2 = fma(Qr, Qr, F.mul(Qi, Qi));
-                    const double inv = kMixed ? rcp_pos_2nd(q2) : rcp_pos(q2);
+                    const double inv = rcp_pos(fma(Qr, Qr, F.mul(Qi, Qi)));
                     cr = F.mul(Qi, inv);
                     ci = F.mul(Qr, inv);
-                    R gr, gi;
-                    if constexpr (kMixed) {
-                        gr = d2f(cr);
-                        gi = d2f(ci);
-                    } else {
-                        gr = cr;
-                        gi = ci;
-                    }
                     const R ur = F.sub(p.x, Di);
                     const R ui = F.add(p.y, Dr);
-                    Dr = fma(gr, ui, F.mul(gi, ur));
-                    Di = fma(gi, ui, F.mul(-gr, ur));
-                    r[lane] = mk(gr, gi);
+                    Dr = fma(cr, ui, F.mul(ci, ur));
+                    Di = fma(ci, ui, F.mul(-cr, ur));
+                    r[lane] = mk(cr, ci);
                     r[kLanes + lane] = mk(Dr, Di);
                     r += 2 * kLanes;
                 }
