@@ -153,6 +153,25 @@ tdse_status tdse_copy_state(tdse_batch* batch, void* buffer_dev, int32_t directi
 tdse_status tdse_adjoint(tdse_batch* batch, const double* E_dev, const double* gd_dev, const double* ga_dev,
                          double* gE_dev, int32_t ckpt_every, void* stream);
 
+/* tdse_propagate that also records the adjoint's checkpoints: the state after every ckpt_every-th
+ * step (and the state at step 0) is copied into the batch's checkpoint buffers, in the layout
+ * tdse_adjoint's own forward pass writes.  A recording starts with step_begin = 0 and may continue
+ * over further calls, each beginning where the previous one ended, with the same ckpt_every; once it
+ * covers every instance's last step, tdse_adjoint_checkpointed can start from it.  FP64 FULL_CN
+ * only.  Allocates the adjoint's buffers on first use (as tdse_adjoint); the arguments are
+ * tdse_propagate's.  TDSE_ERR_STATE for a continuation that does not follow the recording. */
+tdse_status tdse_propagate_checkpointed(tdse_batch* batch, const double* E_dev, double* d_dev, double* a_dev,
+                                        int64_t sample_base, int64_t step_begin, int64_t step_end, int32_t ckpt_every,
+                                        void* stream);
+
+/* tdse_adjoint from the checkpoints of a complete tdse_propagate_checkpointed recording: the same
+ * gradient, without the adjoint's own forward pass (the intervals are recomputed from the recorded
+ * checkpoints, then swept backwards).  E_dev must hold the field of the recorded propagation; the
+ * batch's current state is not used.  TDSE_ERR_STATE when no complete recording exists (none, or
+ * the launch shape or layout changed since). */
+tdse_status tdse_adjoint_checkpointed(tdse_batch* batch, const double* E_dev, const double* gd_dev, const double* ga_dev,
+                                      double* gE_dev, void* stream);
+
 /* Synchronise the stream and report TDSE_ERR_NONFINITE if any instance's norm became non-finite
  * or exceeded 1 + 1e-6 (FP64; 1 + 1e-3 in MIXED) during a propagation since the batch was created
  * or last checked, or TDSE_ERR_TIMEOUT if a bounded bulk-copy wait gave up for it (MIXED, see

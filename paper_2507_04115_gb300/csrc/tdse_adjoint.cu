@@ -14,7 +14,8 @@
 //
 // Memory: the forward states are recomputed from checkpoints every K steps; within a checkpoint
 // interval the pre-mask states psi~ are kept on a per-CTA tape.  One CTA owns a group for the whole
-// call: first a forward pass writing the checkpoints, then the intervals from last to first
+// call: first a forward pass writing the checkpoints (unless a checkpointed forward propagation has
+// written them already, tdse_propagate_checkpointed), then the intervals from last to first
 // (recompute the interval onto the tape, then sweep it backwards).
 //
 // Lane geometry (any group width I = 32/L, see GroupDesc): lane l of warp w holds instance l % I
@@ -179,7 +180,7 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
                   double2* __restrict__ work_all, double2* __restrict__ tape_all, double2* __restrict__ scratch_all,
                   int rows, int n_max, int kc, const double* __restrict__ E, const double* __restrict__ gd,
                   const double* __restrict__ ga, double* __restrict__ gE, int mask_on, int* __restrict__ busy,
-                  int* __restrict__ progress)
+                  int* __restrict__ progress, int have_ckpt)
 {
     extern __shared__ double red[];
     __shared__ int s_g;
@@ -226,17 +227,20 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
         if (nt >= 0)
             for (int64_t n = w * L + geo.q; n <= nt; n += P * L) gE[row + n] = 0.0;
 
-        // forward pass from psi^0, checkpoint every kc steps
-        copy_state(work, psi0_all + G.psi_off, state);
-        copy_state(ck, psi0_all + G.psi_off, state);
-        __syncthreads();
-        for (int64_t n = 0; n < nt_max; ++n) {
-            const bool active = n < nt;
-            const double Eb = active ? 0.5 * (E[row + n] + E[row + n + 1]) : 0.0;
-            fwd_step(work, geo, Eb, tab_ab2, tab_m, jm_lo, jm_hi, sc, active, nullptr);
-            if ((n + 1) % kc == 0 && n + 1 < nt_max) {
-                copy_state(ck + ((n + 1) / kc) * state, work, state);
-                __syncthreads();
+        // forward pass from psi^0, checkpoint every kc steps (skipped when a checkpointed forward
+        // propagation already wrote them)
+        if (!have_ckpt) {
+            copy_state(work, psi0_all + G.psi_off, state);
+            copy_state(ck, psi0_all + G.psi_off, state);
+            __syncthreads();
+            for (int64_t n = 0; n < nt_max; ++n) {
+                const bool active = n < nt;
+                const double Eb = active ? 0.5 * (E[row + n] + E[row + n + 1]) : 0.0;
+                fwd_step(work, geo, Eb, tab_ab2, tab_m, jm_lo, jm_hi, sc, active, nullptr);
+                if ((n + 1) % kc == 0 && n + 1 < nt_max) {
+                    copy_state(ck + ((n + 1) / kc) * state, work, state);
+                    __syncthreads();
+                }
             }
         }
         for (int64_t k = threadIdx.x; k < state; k += blockDim.x) lam[k] = make_double2(0.0, 0.0);
@@ -344,8 +348,9 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
         {
             double s0 = 0.0;
             if (nt == 0) {
+                const double2* p0 = have_ckpt ? ck : psi0_all + G.psi_off;   // psi^0
                 for (int j = geo.s; j < geo.e; ++j) {
-                    const double2 p = ld_cg(psi0_all + G.psi_off + geo.at(j));
+                    const double2 p = ld_cg(p0 + geo.at(j));
                     s0 = fma(p.x, p.x, fma(p.y, p.y, s0));
                 }
             }
@@ -370,7 +375,7 @@ cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, 
                                    const void* d_psi0, void* d_lam, void* d_ckpt, const int64_t* d_ckpt_off,
                                    void* d_work, void* d_tape, void* d_scratch, int rows, int n_max, int kc,
                                    const double* E, const double* gd, const double* ga, double* gE, int mask_on,
-                                   int* d_busy, int* d_progress, cudaStream_t st)
+                                   int* d_busy, int* d_progress, cudaStream_t st, int have_ckpt)
 {
     if (n_groups == 0 || ctas == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(d_busy, 0, sizeof(int) * n_groups, st);
@@ -382,7 +387,7 @@ cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, 
         d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, static_cast<const double2*>(d_psi0),
         static_cast<double2*>(d_lam), static_cast<double2*>(d_ckpt), d_ckpt_off, static_cast<double2*>(d_work),
         static_cast<double2*>(d_tape), static_cast<double2*>(d_scratch), rows, n_max, kc, E, gd, ga, gE, mask_on,
-        d_busy, d_progress);
+        d_busy, d_progress, have_ckpt);
     return cudaGetLastError();
 }
 

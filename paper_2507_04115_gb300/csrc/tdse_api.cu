@@ -126,6 +126,8 @@ struct tdse_batch {
     void* d_work = nullptr;
     void* d_tape = nullptr;
     int adj_kc = 0, adj_ctas = 0;
+    // checkpoints recorded by tdse_propagate_checkpointed: steps [0, ckpt_next) are covered (-1: none)
+    int64_t ckpt_next = -1;
     // energy-distribution buffers (allocated on first use, grown as needed)
     void* d_ed_scratch = nullptr;
     int64_t ed_scratch_elems = 0;
@@ -402,6 +404,7 @@ tdse_status build_groups(tdse_batch* b)
     b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
     b->d_ckpt_off = nullptr;
     b->adj_kc = 0;
+    b->ckpt_next = -1;
     TDSE_CUDA(dev_alloc(&b->d_groups, b->groups.size()), "cudaMalloc(groups)");
     TDSE_CUDA(dev_alloc(&b->d_slot_row, (size_t)b->n_slots), "cudaMalloc(slots)");
     TDSE_CUDA(dev_alloc(&b->d_slot_nt, (size_t)b->n_slots), "cudaMalloc(slots)");
@@ -470,6 +473,51 @@ tdse_status build_plan(tdse_batch* b)
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+namespace {
+
+// Adjoint buffers (lambda, checkpoints and their offsets, the per-CTA work state and tape), sized by
+// the grouping, the persistent grid and the checkpoint interval; reallocated when either changes,
+// which drops any recorded checkpoints.
+tdse_status ensure_adjoint_buffers(tdse_batch* b, int ckpt_every, cudaStream_t st, int* n_max_out)
+{
+    int n_max = 1;
+    for (auto& G : b->groups) n_max = std::max(n_max, G.N);
+    *n_max_out = n_max;
+    if (!b->d_lam || b->adj_kc != ckpt_every || b->adj_ctas != b->ctas) {
+        b->ckpt_next = -1;
+        TDSE_CUDA(cudaStreamSynchronize(st), "tdse_adjoint: synchronize");
+        cudaFree(b->d_lam);
+        cudaFree(b->d_ckpt);
+        cudaFree(b->d_ckpt_off);
+        cudaFree(b->d_work);
+        cudaFree(b->d_tape);
+        b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
+        b->d_ckpt_off = nullptr;
+        b->adj_kc = 0;
+        std::vector<int64_t> off(b->groups.size());
+        int64_t total = 0;
+        for (size_t g = 0; g < b->groups.size(); ++g) {
+            off[g] = total;
+            const int64_t n_int = (b->groups[g].nt_max + ckpt_every - 1) / ckpt_every;
+            total += (n_int + 1) * (int64_t)b->groups[g].N * b->groups[g].I;
+        }
+        const size_t cx = sizeof(double2);
+        TDSE_CUDA(cudaMalloc(&b->d_lam, (size_t)std::max<int64_t>(b->psi_elems, 1) * cx), "cudaMalloc(adjoint lambda)");
+        TDSE_CUDA(cudaMalloc(&b->d_ckpt, (size_t)std::max<int64_t>(total, 1) * cx), "cudaMalloc(adjoint checkpoints)");
+        TDSE_CUDA(dev_alloc(&b->d_ckpt_off, off.size()), "cudaMalloc(adjoint offsets)");
+        TDSE_CUDA(cudaMalloc(&b->d_work, (size_t)b->ctas * n_max * kLanes * cx), "cudaMalloc(adjoint work)");
+        TDSE_CUDA(cudaMalloc(&b->d_tape, (size_t)b->ctas * ckpt_every * (size_t)n_max * kLanes * cx),
+                  "cudaMalloc(adjoint tape)");
+        TDSE_CUDA(cudaMemcpy(b->d_ckpt_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice),
+                  "cudaMemcpy(adjoint offsets)");
+        b->adj_kc = ckpt_every;
+        b->adj_ctas = b->ctas;
+    }
+    return TDSE_OK;
+}
 
 }  // namespace
 
@@ -731,8 +779,8 @@ tdse_status tdse_ground_state(tdse_batch* b, double dtau, int64_t max_iter, doub
     return TDSE_OK;
 }
 
-tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, double* a_dev, int64_t sample_base,
-                           int64_t step_begin, int64_t step_end, void* stream)
+static tdse_status propagate_impl(tdse_batch* b, const double* E_dev, double* d_dev, double* a_dev, int64_t sample_base,
+                                  int64_t step_begin, int64_t step_end, void* stream, int ckpt_every)
 {
     if (!b) return fail(TDSE_ERR_ARG, "tdse_propagate: NULL batch");
     if (!E_dev || !d_dev || !a_dev) return fail(TDSE_ERR_ARG, "tdse_propagate: NULL buffer");
@@ -762,9 +810,16 @@ tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, do
         TDSE_CUDA(launch_propagate_full_cn(b->mixed(), b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas,
                                            b->d_cls, b->d_tab, b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_scratch,
                                            b->rows, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, b->slice,
-                                           b->mask_on, b->d_busy, b->d_progress, b->d_status, b->ring, b->wait_polls, st),
+                                           b->mask_on, b->d_busy, b->d_progress, b->d_status, b->ring, b->wait_polls, st,
+                                           ckpt_every > 0 ? b->d_ckpt : nullptr, b->d_ckpt_off, ckpt_every),
                   "propagate launch");
     return TDSE_OK;
+}
+
+tdse_status tdse_propagate(tdse_batch* b, const double* E_dev, double* d_dev, double* a_dev, int64_t sample_base,
+                           int64_t step_begin, int64_t step_end, void* stream)
+{
+    return propagate_impl(b, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, stream, 0);
 }
 
 static tdse_status locate(const tdse_batch* b, int64_t inst, int64_t* off, int* N, int* lane, int* I)
@@ -862,36 +917,9 @@ tdse_status tdse_adjoint(tdse_batch* b, const double* E_dev, const double* gd_de
     if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t st = (cudaStream_t)stream;
     int n_max = 1;
-    for (auto& G : b->groups) n_max = std::max(n_max, G.N);
-    if (!b->d_lam || b->adj_kc != ckpt_every || b->adj_ctas != b->ctas) {
-        TDSE_CUDA(cudaStreamSynchronize(st), "tdse_adjoint: synchronize");
-        cudaFree(b->d_lam);
-        cudaFree(b->d_ckpt);
-        cudaFree(b->d_ckpt_off);
-        cudaFree(b->d_work);
-        cudaFree(b->d_tape);
-        b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
-        b->d_ckpt_off = nullptr;
-        b->adj_kc = 0;
-        std::vector<int64_t> off(b->groups.size());
-        int64_t total = 0;
-        for (size_t g = 0; g < b->groups.size(); ++g) {
-            off[g] = total;
-            const int64_t n_int = (b->groups[g].nt_max + ckpt_every - 1) / ckpt_every;
-            total += (n_int + 1) * (int64_t)b->groups[g].N * b->groups[g].I;
-        }
-        const size_t cx = sizeof(double2);
-        TDSE_CUDA(cudaMalloc(&b->d_lam, (size_t)std::max<int64_t>(b->psi_elems, 1) * cx), "cudaMalloc(adjoint lambda)");
-        TDSE_CUDA(cudaMalloc(&b->d_ckpt, (size_t)std::max<int64_t>(total, 1) * cx), "cudaMalloc(adjoint checkpoints)");
-        TDSE_CUDA(dev_alloc(&b->d_ckpt_off, off.size()), "cudaMalloc(adjoint offsets)");
-        TDSE_CUDA(cudaMalloc(&b->d_work, (size_t)b->ctas * n_max * kLanes * cx), "cudaMalloc(adjoint work)");
-        TDSE_CUDA(cudaMalloc(&b->d_tape, (size_t)b->ctas * ckpt_every * (size_t)n_max * kLanes * cx),
-                  "cudaMalloc(adjoint tape)");
-        TDSE_CUDA(cudaMemcpy(b->d_ckpt_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice),
-                  "cudaMemcpy(adjoint offsets)");
-        b->adj_kc = ckpt_every;
-        b->adj_ctas = b->ctas;
-    }
+    tdse_status s = ensure_adjoint_buffers(b, ckpt_every, st, &n_max);
+    if (s != TDSE_OK) return s;
+    b->ckpt_next = -1;   // the adjoint's own forward pass rewrites the checkpoints
     TDSE_CUDA(launch_adjoint_full_cn(b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas, b->d_cls, b->d_tab,
                                      b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_lam, b->d_ckpt, b->d_ckpt_off,
                                      b->d_work, b->d_tape, b->d_scratch, b->rows, n_max, ckpt_every, E_dev, gd_dev,
@@ -899,6 +927,68 @@ tdse_status tdse_adjoint(tdse_batch* b, const double* E_dev, const double* gd_de
               "adjoint launch");
     return TDSE_OK;
 }
+
+tdse_status tdse_propagate_checkpointed(tdse_batch* b, const double* E_dev, double* d_dev, double* a_dev,
+                                        int64_t sample_base, int64_t step_begin, int64_t step_end, int32_t ckpt_every,
+                                        void* stream)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_propagate_checkpointed: NULL batch");
+    if (b->precision != TDSE_FP64 || b->scheme != TDSE_FULL_CN)
+        return fail(TDSE_ERR_ARG, "tdse_propagate_checkpointed: only FP64 FULL_CN batches have an adjoint");
+    if (ckpt_every < 1 || ckpt_every > 65536) return fail(TDSE_ERR_ARG, "tdse_propagate_checkpointed: ckpt_every out of [1, 65536]");
+    if (step_begin != 0 && (b->ckpt_next != step_begin || b->adj_kc != ckpt_every))
+        return fail(TDSE_ERR_STATE, "tdse_propagate_checkpointed: a recording starts at step 0 and continues where the "
+                                    "previous checkpointed call ended, with the same ckpt_every");
+    {
+        DeviceGuard guard(b->device);
+        if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+        int n_max = 1;
+        const int64_t before = b->ckpt_next;
+        tdse_status s = ensure_adjoint_buffers(b, ckpt_every, (cudaStream_t)stream, &n_max);
+        if (s != TDSE_OK) return s;
+        if (step_begin != 0 && b->ckpt_next != before)
+            return fail(TDSE_ERR_STATE, "tdse_propagate_checkpointed: the launch shape changed during the recording");
+    }
+    tdse_status s = propagate_impl(b, E_dev, d_dev, a_dev, sample_base, step_begin, step_end, stream, ckpt_every);
+    if (s != TDSE_OK) {
+        b->ckpt_next = -1;
+        return s;
+    }
+    b->ckpt_next = step_end;
+    return TDSE_OK;
+}
+
+tdse_status tdse_adjoint_checkpointed(tdse_batch* b, const double* E_dev, const double* gd_dev, const double* ga_dev,
+                                      double* gE_dev, void* stream)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_adjoint_checkpointed: NULL batch");
+    if (!E_dev || !gd_dev || !ga_dev || !gE_dev) return fail(TDSE_ERR_ARG, "tdse_adjoint_checkpointed: NULL buffer");
+    if (b->precision != TDSE_FP64 || b->scheme != TDSE_FULL_CN)
+        return fail(TDSE_ERR_ARG, "tdse_adjoint_checkpointed: only FP64 FULL_CN batches have an adjoint");
+    for (int64_t i = 0; i < b->n_inst; ++i)
+        if (b->row_off[i + 1] - b->row_off[i] < b->n_steps[i] + 1)
+            return fail(TDSE_ERR_ARG, "tdse_adjoint_checkpointed: row of instance " + std::to_string(i) + " shorter than Nt + 1");
+    if (b->adj_kc < 1) return fail(TDSE_ERR_STATE, "tdse_adjoint_checkpointed: nothing recorded");
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    int n_max = 1;
+    // the recording allocated the buffers; a changed launch shape reallocates them and drops it
+    tdse_status s = ensure_adjoint_buffers(b, b->adj_kc, st, &n_max);
+    if (s != TDSE_OK) return s;
+    int64_t nt_all = 0;
+    for (int64_t i = 0; i < b->n_inst; ++i) nt_all = std::max(nt_all, b->n_steps[i]);
+    if (b->ckpt_next < nt_all || !b->d_ckpt)
+        return fail(TDSE_ERR_STATE, "tdse_adjoint_checkpointed: no complete checkpointed forward propagation "
+                                    "(tdse_propagate_checkpointed from step 0 through every instance's last step)");
+    TDSE_CUDA(launch_adjoint_full_cn(b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas, b->d_cls, b->d_tab,
+                                     b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_lam, b->d_ckpt, b->d_ckpt_off,
+                                     b->d_work, b->d_tape, b->d_scratch, b->rows, n_max, b->adj_kc, E_dev, gd_dev,
+                                     ga_dev, gE_dev, b->mask_on, b->d_busy, b->d_progress, st, 1),
+              "adjoint launch");
+    return TDSE_OK;
+}
+
 
 tdse_status tdse_energy_distribution(tdse_batch* b, const double* E_grid_host, int32_t n_energies, double epsilon,
                                      double* P_dev, void* stream)

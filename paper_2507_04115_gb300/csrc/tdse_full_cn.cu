@@ -36,7 +36,7 @@ namespace tdse {
 // K .. K + m - 1.  Observables are summed over the L lanes of an instance by shuffles, then over the
 // warps.  No bulk copies on this path (it serves small batches, where the FP64 elimination is the
 // bound in both precisions); MIXED sums the observables in double directly.
-template <bool kMixed>
+template <bool kMixed, bool kCkpt>
 __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, typename Prec<kMixed>::C* __restrict__ ps,
                                             const double2* __restrict__ tab_ab2, const double2* __restrict__ tab_xv2,
                                             const double* __restrict__ tab_m, double inv_beta,
@@ -44,7 +44,8 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, 
                                             int64_t nt, int64_t row, int64_t slot, int64_t n0, int64_t n1,
                                             bool initial, const double* __restrict__ E, double* __restrict__ d_out,
                                             double* __restrict__ a_out, int64_t sample_base,
-                                            typename Prec<kMixed>::C* __restrict__ sc, double* red, int* status)
+                                            typename Prec<kMixed>::C* __restrict__ sc, double* red, int* status,
+                                            double2* __restrict__ ck, int kc)
 {
     using R = typename Prec<kMixed>::R;
     using Cx = typename Prec<kMixed>::C;
@@ -84,6 +85,9 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, 
             d_out[row - sample_base] = t.x * dx;
             a_out[row - sample_base] = fma(E0, t.n, t.v) * dx;
         }
+        if constexpr (kCkpt)   // checkpoint 0: the initial state (each lane copies its own points)
+            if (w < G.P)
+                for (int j = s_own; j < e_own; ++j) ck[(int64_t)j * I + i] = ld_cg(ps + (int64_t)j * I + i);
         __syncthreads();
     }
 
@@ -179,6 +183,11 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, 
             a_out[kk] = fma(En1, t.n, t.v) * dx;
             if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
         }
+        if constexpr (kCkpt)   // checkpoint (n + 1)/kc of the adjoint's recomputation
+            if ((n + 1) % kc == 0 && n + 1 < G.nt_max && w < G.P) {
+                double2* dst = ck + ((n + 1) / kc) * ((int64_t)N * I);
+                for (int j = s_own; j < e_own; ++j) dst[(int64_t)j * I + i] = ld_cg(ps + (int64_t)j * I + i);
+            }
     }
 }
 
@@ -199,14 +208,15 @@ __device__ __forceinline__ void fwd_row_f32(float2 t, float2 p, float Eb, float 
     Dr = nDr;
 }
 
-template <bool kMixed>
+template <bool kMixed, bool kCkpt>
 __global__ void __launch_bounds__(512, 1)
 k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const ClassDesc* __restrict__ cls,
                     const double* __restrict__ tab, const int64_t* __restrict__ slot_row,
                     const int64_t* __restrict__ slot_nt, void* __restrict__ psi_raw, void* __restrict__ scratch_raw,
                     int rows, const double* __restrict__ E, double* __restrict__ d_out, double* __restrict__ a_out,
                     int64_t sample_base, int64_t step_begin, int64_t step_end, int slice, int mask_on,
-                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status, int ring_slots, uint32_t wait_polls)
+                    int* __restrict__ busy, int* __restrict__ progress, int* __restrict__ status, int ring_slots, uint32_t wait_polls,
+                    double2* __restrict__ ckpt, const int64_t* __restrict__ ckpt_off, int kc)
 {
     using R = typename Prec<kMixed>::R;
     using Cx = typename Prec<kMixed>::C;
@@ -275,9 +285,9 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const int64_t n1 = min(n_end, n0 + slice);
 
         if (G.I != kLanes) {
-            split_slice<kMixed>(G, F, ps, tab_ab2, tab_xv2, tab_m, inv_beta, two_over_beta, dx, jm_lo, jm_hi,
-                                nt, row, slot, n0, n1, kslice == 0 && step_begin == 0, E, d_out, a_out,
-                                sample_base, sc, red, status);
+            split_slice<kMixed, kCkpt>(G, F, ps, tab_ab2, tab_xv2, tab_m, inv_beta, two_over_beta, dx, jm_lo, jm_hi,
+                                       nt, row, slot, n0, n1, kslice == 0 && step_begin == 0, E, d_out, a_out,
+                                       sample_base, sc, red, status, kCkpt ? ckpt + ckpt_off[g] : nullptr, kc);
         } else {
         if (kslice == 0 && step_begin == 0) {
             // observables of the initial state
@@ -295,6 +305,10 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 const double E0 = E[row - sample_base];
                 d_out[row - sample_base] = t.x * dx;
                 a_out[row - sample_base] = fma(E0, t.n, t.v) * dx;
+            }
+            if constexpr (kCkpt && !kMixed) {   // checkpoint 0: the initial state (own rows)
+                double2* dst = ckpt + ckpt_off[g];
+                for (int j = s; j < e; ++j) dst[(int64_t)j * kLanes + lane] = ld_cg(ps + (int64_t)j * kLanes + lane);
             }
             __syncthreads();
         }
@@ -585,6 +599,11 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 // covers rounding: 1e-6 in FP64, 1e-3 in MIXED where float psi random-walks ~1e-5
                 if (!(t.n * dx <= (kMixed ? 1.0 + 1e-3 : 1.0 + 1e-6))) status[slot] = 1;
             }
+            if constexpr (kCkpt && !kMixed)   // checkpoint (n + 1)/kc of the adjoint's recomputation
+                if ((n + 1) % kc == 0 && n + 1 < G.nt_max) {
+                    double2* dst = ckpt + ckpt_off[g] + ((n + 1) / kc) * ((int64_t)N * kLanes);
+                    for (int j = s; j < e; ++j) dst[(int64_t)j * kLanes + lane] = ld_cg(ps + (int64_t)j * kLanes + lane);
+                }
         }
         }   // 32-wide group
 
@@ -607,9 +626,11 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
                                      const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
                                      const double* E, double* d_out, double* a_out, int64_t sample_base,
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
-                                     int* d_progress, int* d_status, int ring, uint32_t wait_polls, cudaStream_t st)
+                                     int* d_progress, int* d_status, int ring, uint32_t wait_polls, cudaStream_t st,
+                                     void* d_ckpt, const int64_t* d_ckpt_off, int kc)
 {
     if (n_groups == 0 || ctas == 0) return cudaSuccess;
+    if (d_ckpt && (mixed || kc < 1)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(d_busy, 0, sizeof(int) * n_groups, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d_progress, 0, sizeof(int) * n_groups, st);
@@ -620,18 +641,25 @@ cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64
         static std::atomic<bool> attr_set[kMaxAttrDevices];
         int dev = 0;
         if (attr_needed(attr_set, &dev)) {
-            e = cudaFuncSetAttribute(k_propagate_full_cn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_propagate_full_cn<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)full_cn_smem_max_bytes());
             if (e != cudaSuccess) return e;
             attr_done(attr_set, dev);
         }
-        k_propagate_full_cn<true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
+        k_propagate_full_cn<true, false><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
-            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring, wait_polls);
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring, wait_polls,
+            nullptr, nullptr, 0);
+    } else if (d_ckpt) {
+        k_propagate_full_cn<false, true><<<(unsigned)ctas, P * kLanes, smem, st>>>(
+            d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring, wait_polls,
+            static_cast<double2*>(d_ckpt), d_ckpt_off, kc);
     } else {
-        k_propagate_full_cn<false><<<(unsigned)ctas, P * kLanes, smem, st>>>(
+        k_propagate_full_cn<false, false><<<(unsigned)ctas, P * kLanes, smem, st>>>(
             d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, d_psi, d_scratch, rows, E, d_out, a_out,
-            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring, wait_polls);
+            sample_base, step_begin, step_end, slice, mask_on, d_busy, d_progress, d_status, ring, wait_polls,
+            nullptr, nullptr, 0);
     }
     return cudaGetLastError();
 }
@@ -643,13 +671,13 @@ int propagate_max_ctas_per_sm(int mixed, int P)
     int n = 0;
     const size_t smem = full_cn_smem_bytes(mixed, P, kMinRing);   // the shallowest ring
     if (mixed &&
-        cudaFuncSetAttribute(k_propagate_full_cn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_propagate_full_cn<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)full_cn_smem_max_bytes()) != cudaSuccess) {
         cudaGetLastError();   // do not leave the failure for the next launch check
         return 1;
     }
-    const cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<true>, P * kLanes, smem)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<false>, P * kLanes, smem);
+    const cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<true, false>, P * kLanes, smem)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate_full_cn<false, false>, P * kLanes, smem);
     if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

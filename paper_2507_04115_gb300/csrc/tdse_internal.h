@@ -142,14 +142,17 @@ cudaError_t launch_broadcast_psi(int mixed, const GroupDesc* d_groups, int64_t n
 // dynamically, `slice` steps at a time.  mixed = 0: psi and scratch are double2; mixed = 1:
 // float2.  Scratch holds ctas * P * rows rows of 2 * 32 complex values.  ring: MIXED bulk-copy
 // slots per warp in [2, 4] (full_cn_ring_slots for the CTAs per SM of the launch); wait_polls:
-// polls before a MIXED bulk-copy wait gives up (the batch reports TDSE_ERR_TIMEOUT).
+// polls before a MIXED bulk-copy wait gives up (the batch reports TDSE_ERR_TIMEOUT).  d_ckpt (FP64
+// only, NULL = none): the state after every kc-th step is also written to the adjoint's checkpoint
+// layout (group g at d_ckpt_off[g], checkpoint c at + c * N * I; c = 0 is the state at step 0).
 cudaError_t launch_propagate_full_cn(int mixed, const GroupDesc* d_groups, int64_t n_groups, int P, int ctas,
                                      const ClassDesc* d_cls, const double* d_tab, const int64_t* d_slot_row,
                                      const int64_t* d_slot_nt, void* d_psi, void* d_scratch, int rows,
                                      const double* E, double* d_out, double* a_out, int64_t sample_base,
                                      int64_t step_begin, int64_t step_end, int slice, int mask_on, int* d_busy,
                                      int* d_progress, int* d_status, int ring, uint32_t wait_polls,
-                                     cudaStream_t st);
+                                     cudaStream_t st, void* d_ckpt = nullptr, const int64_t* d_ckpt_off = nullptr,
+                                     int kc = 0);
 // CTAs of P warps that fit on one SM (MIXED: with the shallowest bulk-copy ring).
 int propagate_max_ctas_per_sm(int mixed, int P);
 // MIXED bulk-copy slots per warp when per_sm CTAs of P warps share an SM.
@@ -163,7 +166,7 @@ cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, 
                                    const void* d_psi0, void* d_lam, void* d_ckpt, const int64_t* d_ckpt_off,
                                    void* d_work, void* d_tape, void* d_scratch, int rows, int n_max, int kc,
                                    const double* E, const double* gd, const double* ga, double* gE, int mask_on,
-                                   int* d_busy, int* d_progress, cudaStream_t st);
+                                   int* d_busy, int* d_progress, cudaStream_t st, int have_ckpt = 0);
 
 // Energy distribution of every instance state (tdse_resolvent.cu): pivots per (class, energy) into
 // d_piv (2 * piv_elems complex doubles, class c at d_piv_off[c], N_c rows of nE rounded up to 32),

@@ -23,6 +23,7 @@ EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
            "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_model_layout",
            "tdse_populations", "tdse_ionisation", "tdse_dipole_spectrum", "tdse_hankel",
+           "tdse_propagate_checkpointed", "tdse_adjoint_checkpointed",
            "tdse_last_error")
 
 
@@ -95,6 +96,9 @@ def load(path: str | None = None):
     L.tdse_probe_pipes.argtypes = [ctypes.c_int, ctypes.POINTER(tdse_pipe_rates)]
     L.tdse_copy_state.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
     L.tdse_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp]
+    L.tdse_propagate_checkpointed.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.c_int32, _vp]
+    L.tdse_adjoint_checkpointed.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.tdse_autotune.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.POINTER(tdse_tune_trial), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp]
     L.tdse_set_layout.argtypes = [_vp, ctypes.c_int32]
@@ -327,6 +331,24 @@ class Batch:
                                    _dev_ptr(gE, "gE"), int(ckpt_every), _stream_ptr(stream)))
         return gE
 
+    def propagate_checkpointed(self, E, d, a, ckpt_every=256, step_begin=0, step_end=None, sample_base=0,
+                               stream=None):
+        """tdse_propagate that also records the adjoint's checkpoints (see tdse_propagate_checkpointed)."""
+        if step_end is None:
+            step_end = int(self.n_steps.max())
+        _check(load().tdse_propagate_checkpointed(self._h, _dev_ptr(E, "E"), _dev_ptr(d, "d"), _dev_ptr(a, "a"),
+                                                  int(sample_base), int(step_begin), int(step_end), int(ckpt_every),
+                                                  _stream_ptr(stream)))
+
+    def adjoint_checkpointed(self, E, gd, ga, gE=None, stream=None):
+        """dL/dE from the last complete checkpointed propagation (see tdse_adjoint_checkpointed)."""
+        import torch
+        if gE is None:
+            gE = torch.zeros_like(E)
+        _check(load().tdse_adjoint_checkpointed(self._h, _dev_ptr(E, "E"), _dev_ptr(gd, "gd"), _dev_ptr(ga, "ga"),
+                                                _dev_ptr(gE, "gE"), _stream_ptr(stream)))
+        return gE
+
     def autotune(self, E, d, a, step_begin=0, step_end=None, sample_base=0, repeats=1, stream=None):
         """Time candidate launch shapes on steps [step_begin, step_end) of the field rows E (d and a
         rows there are overwritten) and keep the fastest (see tdse_autotune).  The batch's state is
@@ -478,8 +500,10 @@ def _make_autograd():
 
     class TDSEPropagate(torch.autograd.Function):
         """(d, a) = propagate(E) for an FP64 FULL_CN batch, differentiable with respect to the field
-        samples E through the library's adjoint kernel.  The batch must hold the initial state; it is
-        restored after the forward pass so that the backward pass starts from the same psi^0."""
+        samples E through the library's adjoint kernel.  The batch must hold the initial state; the
+        forward pass records the adjoint's checkpoints (so the backward pass recomputes only from them)
+        and the initial state is restored afterwards.  The recording belongs to the batch: run each
+        forward's backward before the next forward on the same batch."""
 
         @staticmethod
         def forward(ctx, E, batch, ckpt_every):
@@ -487,7 +511,7 @@ def _make_autograd():
             psi0 = batch.save_state()
             d = torch.zeros_like(E)
             a = torch.zeros_like(E)
-            batch.propagate(E, d, a)
+            batch.propagate_checkpointed(E, d, a, ckpt_every)
             batch.load_state(psi0)
             ctx.batch = batch
             ctx.ckpt_every = ckpt_every
@@ -499,7 +523,7 @@ def _make_autograd():
             (E,) = ctx.saved_tensors
             gd = torch.zeros_like(E) if gd is None else gd.contiguous()
             ga = torch.zeros_like(E) if ga is None else ga.contiguous()
-            gE = ctx.batch.adjoint(E, gd, ga, ckpt_every=ctx.ckpt_every)
+            gE = ctx.batch.adjoint_checkpointed(E, gd, ga)
             return gE, None, None
 
     return TDSEPropagate

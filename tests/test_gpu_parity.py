@@ -576,6 +576,58 @@ def test_adjoint_matches_oracle_and_finite_differences(env, lanes):
     b1.close()
 
 
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_checkpointed_adjoint_equals_adjoint(env, lanes):
+    """tdse_adjoint_checkpointed from a recording made by tdse_propagate_checkpointed in two chunks
+    gives tdse_adjoint's gradient (the checkpoints come from the forward kernel instead of the
+    adjoint's own forward pass: the same states to rounding) and the oracle's; calls out of order
+    are refused."""
+    tdse, oracle = env
+    from paper_2507_04115_gb300 import inputs
+    rng = np.random.default_rng(33)
+    n = 35
+    N, dx, dt, a = 384, 0.2, 0.05, 1.19
+    nt = rng.integers(150, 300, n)
+    nt[7] = 0
+    rows = [inputs.sin2_pulse(int(k), dt, rng.uniform(0.04, 0.09), 0.057, 1.0, rng.uniform(0, 6)) for k in nt]
+    offs = np.concatenate([[0], np.cumsum(nt + 1)])
+    dev = torch.device("cuda", 0)
+    Et = _device_rows(rows, offs, dev)
+    gd = torch.from_numpy(rng.standard_normal(int(offs[-1]))).to(dev)
+    ga = torch.from_numpy(rng.standard_normal(int(offs[-1]))).to(dev)
+    b = tdse.Batch([N] * n, dx, a, nt, dt, row_offsets=offs, absorber=(20.0, 0.125), lanes_per_instance=lanes)
+    b.set_launch(3, 1, 0, 1 if lanes == 1 else 2)
+    b.ground_state(**GS_KW)
+    with pytest.raises(tdse.TDSEError) as ei:
+        b.adjoint_checkpointed(Et, gd, ga)                      # nothing recorded yet
+    assert ei.value.status == tdse.TDSE_ERR_STATE
+    psi0 = b.save_state()
+    ref = b.adjoint(Et, gd, ga, ckpt_every=37).cpu().numpy()
+    d, acc = torch.zeros_like(Et), torch.zeros_like(Et)
+    b.propagate_checkpointed(Et, d, acc, 37, 0, 120)
+    with pytest.raises(tdse.TDSEError) as ei:
+        b.adjoint_checkpointed(Et, gd, ga)                      # recording incomplete
+    assert ei.value.status == tdse.TDSE_ERR_STATE
+    with pytest.raises(tdse.TDSEError) as ei:
+        b.propagate_checkpointed(Et, d, acc, 37, 130, 200)      # does not continue the recording
+    assert ei.value.status == tdse.TDSE_ERR_STATE
+    b.propagate_checkpointed(Et, d, acc, 37, 120, 1000)
+    b.load_state(psi0)                                          # the current state is not used
+    gE = b.adjoint_checkpointed(Et, gd, ga).cpu().numpy()
+    torch.cuda.synchronize()
+    for i in range(n):
+        sl = slice(offs[i], offs[i + 1])
+        assert _rel(gE[sl], ref[sl]) < 1e-12, i
+    psi_o, _, _ = oracle.ground_state(N, dx, a, **GS_KW)
+    m = oracle.mask(N, dx, 20.0, 0.125)
+    gdh, gah = gd.cpu().numpy(), ga.cpu().numpy()
+    for i in (0, 7, n - 1):
+        sl = slice(offs[i], offs[i + 1])
+        g_o = oracle.adjoint(psi_o, rows[i], dx, dt, a, gdh[sl], gah[sl], mask_values=m)
+        assert _rel(gE[sl], g_o) < RTOL_SERIES, i
+    b.close()
+
+
 # ------------------------------------------------------------------------------- uneven batches, graphs
 
 def test_uneven_batch_like_the_uneven_workload(env):
