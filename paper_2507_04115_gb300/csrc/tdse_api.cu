@@ -612,7 +612,7 @@ tdse_status tdse_batch_create(const tdse_instance* inst_host, int64_t n_inst, do
     std::vector<int64_t> gs_off(n_cls);
     for (int c = 0; c < n_cls; ++c) {
         gs_off[c] = gs_total;
-        gs_total += 4 * (int64_t)b->classes[c].N;
+        gs_total += kGsWork * (int64_t)b->classes[c].N;
     }
     if ((e = dev_alloc(&b->d_gs_work, (size_t)gs_total)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));
     if ((e = dev_alloc(&b->d_gs_off, (size_t)n_cls)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(gs)"));

@@ -127,8 +127,11 @@ int batch_device(const tdse_batch* b);
 cudaError_t launch_build_tables(const ClassDesc* d_cls, int n_cls, int max_N, double dt, double mask_width,
                                 double mask_exp, int mask_on, double* d_tab, cudaStream_t st);
 
-// Imaginary-time ground state, one CTA per class.  Work buffers: 4 * N doubles per class at
-// work + cls_work_off[c].  Results: psi0 (N doubles per class at the same offsets / 4), energy, iters.
+// Imaginary-time ground state, one CTA of kGsThreads threads per class.  Work buffers: kGsWork * N
+// doubles per class at work + cls_work_off[c], the ground state psi0 in the first N.  Results:
+// psi0, energy, iters.
+constexpr int kGsThreads = 1024;
+constexpr int kGsWork = 8;
 cudaError_t launch_ground_state(const ClassDesc* d_cls, int n_cls, int scheme, double dtau, int64_t max_iter,
                                 double tol, double* d_work, const int64_t* d_work_off, double* d_energy,
                                 int64_t* d_iters, cudaStream_t st);

@@ -72,24 +72,77 @@ cudaError_t launch_build_tables(const ClassDesc* d_cls, int n_cls, int max_N, do
 
 // ------------------------------------------------------------------------------------ ground state
 
+// First-order linear recurrence x_j = a_j x_{j-1} + b_j over j = 0..N-1 with x_{-1} = 0 (rev: over
+// j = N-1..0 with x_N = 0), solved in place by the whole block (x holds b on entry, the solution on
+// exit): each thread runs the recurrence over its chunk of the index range from zero, the chunk maps
+// x_out = P x_in + v (P the product of the chunk's a) are composed by an inclusive scan over the
+// threads, and each chunk adds its incoming value times the running product of its a.  The result
+// equals the sequential sweep up to the order of rounding.  sp, sv: blockDim.x doubles each.
+__device__ void block_recurrence(double* __restrict__ x, const double* __restrict__ a, int N, bool rev, double* sp,
+                                 double* sv)
+{
+    const int T = blockDim.x, t = threadIdx.x;
+    const int c = (N + T - 1) / T;
+    const int k0 = min(N, t * c), k1 = min(N, k0 + c);
+    double y = 0.0, P = 1.0;
+    for (int k = k0; k < k1; ++k) {
+        const int j = rev ? N - 1 - k : k;
+        y = fma(a[j], y, x[j]);
+        P *= a[j];
+        x[j] = y;
+    }
+    sp[t] = P;
+    sv[t] = y;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        double pl = 1.0, vl = 0.0;
+        if (t >= off) {
+            pl = sp[t - off];
+            vl = sv[t - off];
+        }
+        __syncthreads();
+        if (t >= off) {
+            const double pr = sp[t], vr = sv[t];
+            sp[t] = pr * pl;
+            sv[t] = fma(pr, vl, vr);
+        }
+        __syncthreads();
+    }
+    const double carry = t > 0 ? sv[t - 1] : 0.0;   // x at the end of the previous chunk
+    double Q = 1.0;
+    for (int k = k0; k < k1; ++k) {
+        const int j = rev ? N - 1 - k : k;
+        Q *= a[j];
+        x[j] = fma(Q, carry, x[j]);
+    }
+    __syncthreads();
+}
+
 // Imaginary-time Crank-Nicolson for the field-free Hamiltonian of one class per CTA.
 //   FULL_CN  : A = 1 + dtau/2 H0,   y = A^{-1} psi,       psi' = 2 y - psi
 //   NUMEROV  : A = M2 + dtau/2 K,   y = A^{-1} (M2 psi),  psi' = 2 y - psi   (K = -Delta2/2 + M2 V)
 // since A + B = 2M with B = M - dtau/2 K.  Then psi' is normalised and E = <psi|H0|psi> dx.
-// The tridiagonal sweeps run in thread 0 over global work arrays (the ground state is computed
-// once per class); normalisation and energy use the whole block.
-// Work block per class (4N doubles): psi | inverse pivots w | lower multipliers l | y.
+// A is factored once (Thomas pivots, thread 0); every iteration's solve is then two first-order
+// linear recurrences with fixed coefficients, solved block-parallel (block_recurrence), as are the
+// two sweeps of Numerov's M2 solve in the energy.
+// Work block per class (kGsWork N doubles): psi | 1/pivot of A | forward a | backward a | y |
+// 1/pivot of M2 | M2 forward a | M2 backward a.
 __global__ void k_ground_state(const ClassDesc* cls, int scheme, double dtau, int64_t max_iter, double tol,
                                double* work, const int64_t* work_off, double* energy, int64_t* iters)
 {
     __shared__ double red[32];
+    __shared__ double sp[kGsThreads], sv[kGsThreads];
     __shared__ int stop;
     const ClassDesc C = cls[blockIdx.x];
     const int N = C.N;
     double* psi = work + work_off[blockIdx.x];
     double* w = psi + N;
-    double* l = w + N;
-    double* y = l + N;
+    double* fa = w + N;
+    double* ba = fa + N;
+    double* y = ba + N;
+    double* mw = y + N;
+    double* mfa = mw + N;
+    double* mba = mfa + N;
     const double inv_dx2 = 1.0 / (C.dx * C.dx);
     const double c = 0.5 * dtau;
     const bool numerov = (scheme == 1);
@@ -105,19 +158,33 @@ __global__ void k_ground_state(const ClassDesc* cls, int scheme, double dtau, in
     auto A_lo = [&](int j) { return numerov ? 1.0 / 12.0 + c * (-0.5 * inv_dx2 + V_at(j - 1) / 12.0) : -c * 0.5 * inv_dx2; };
     auto A_up = [&](int j) { return numerov ? 1.0 / 12.0 + c * (-0.5 * inv_dx2 + V_at(j + 1) / 12.0) : -c * 0.5 * inv_dx2; };
 
-    // initial state exp(-x^2) and the LU factors of A (Thomas): w_j = 1/(di_j - lo_j up_{j-1} w_{j-1}),
-    // l_j = lo_j w_{j-1} ... stored as w (inverse pivot) and the products needed by the sweeps.
+    // initial state exp(-x^2); the Thomas factors of A: w_j = 1/(di_j - lo_j up_{j-1} w_{j-1}), and
+    // the recurrence coefficients of the two sweeps, forward y_j = w_j r_j - lo_j w_j y_{j-1} and
+    // backward y_j = y_j - up_j w_j y_{j+1}; for Numerov also those of M2 = tridiag(1, 10, 1)/12
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const double x = (j - 0.5 * (N - 1)) * C.dx;
         psi[j] = exp(-x * x);
     }
     if (threadIdx.x == 0) {
-        double wprev = 0.0;
+        double wprev = 0.0, mprev = 0.0;
         for (int j = 0; j < N; ++j) {
             const double piv = j == 0 ? A_di(0) : A_di(j) - A_lo(j) * A_up(j - 1) * wprev;
             w[j] = 1.0 / piv;
-            l[j] = j == 0 ? 0.0 : A_lo(j);
             wprev = w[j];
+            if (numerov) {
+                const double mp = 10.0 / 12.0 - (j > 0 ? (1.0 / 144.0) * mprev : 0.0);
+                mw[j] = 1.0 / mp;
+                mprev = mw[j];
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        fa[j] = j == 0 ? 0.0 : -A_lo(j) * w[j];
+        ba[j] = j == N - 1 ? 0.0 : -A_up(j) * w[j];
+        if (numerov) {
+            mfa[j] = j == 0 ? 0.0 : -(1.0 / 12.0) * mw[j];
+            mba[j] = j == N - 1 ? 0.0 : -(1.0 / 12.0) * mw[j];
         }
     }
     __syncthreads();
@@ -125,29 +192,17 @@ __global__ void k_ground_state(const ClassDesc* cls, int scheme, double dtau, in
     double e_prev = 0.0, e = 0.0;
     int64_t it = 1;
     for (;; ++it) {
-        // right-hand side r = psi (FD) or M2 psi (Numerov), kept in y
+        // right-hand side w_j r_j with r = psi (FD) or M2 psi (Numerov), then the two sweeps
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
             double r = psi[j];
             if (numerov) {
                 r = (10.0 / 12.0) * psi[j] + ((j > 0 ? psi[j - 1] : 0.0) + (j < N - 1 ? psi[j + 1] : 0.0)) / 12.0;
             }
-            y[j] = r;
+            y[j] = w[j] * r;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            // forward: y_j <- (r_j - lo_j y_{j-1}) w_j ; backward: y_j <- y_j - up_j w_j y_{j+1}
-            double prev = 0.0;
-            for (int j = 0; j < N; ++j) {
-                prev = (y[j] - l[j] * prev) * w[j];
-                y[j] = prev;
-            }
-            double nxt = 0.0;
-            for (int j = N - 1; j >= 0; --j) {
-                nxt = y[j] - (j < N - 1 ? A_up(j) * w[j] * nxt : 0.0);
-                y[j] = nxt;
-            }
-        }
-        __syncthreads();
+        block_recurrence(y, fa, N, false, sp, sv);
+        block_recurrence(y, ba, N, true, sp, sv);
         double s = 0.0;
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
             const double v = 2.0 * y[j] - psi[j];
@@ -160,34 +215,17 @@ __global__ void k_ground_state(const ClassDesc* cls, int scheme, double dtau, in
         // energy: kinetic part T psi = -Delta2/2 psi (FD) or M2^{-1}(-Delta2/2 psi) (Numerov)
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
             const double lap = ((j > 0 ? psi[j - 1] : 0.0) - 2.0 * psi[j] + (j < N - 1 ? psi[j + 1] : 0.0)) * inv_dx2;
-            y[j] = -0.5 * lap;
+            y[j] = -0.5 * lap * (numerov ? mw[j] : 1.0);
         }
         __syncthreads();
-        if (numerov && threadIdx.x == 0) {
-            // solve M2 t = y in place (constant-coefficient Thomas, coefficients recomputed on the fly)
-            double cp_prev = 0.0, prev = 0.0;
-            for (int j = 0; j < N; ++j) {
-                const double piv = 10.0 / 12.0 - (j > 0 ? (1.0 / 12.0) * cp_prev : 0.0);
-                const double cp = (1.0 / 12.0) / piv;
-                prev = (y[j] - (j > 0 ? (1.0 / 12.0) * prev : 0.0)) / piv;
-                y[j] = prev;
-                l[j] = cp;   // l is free once the solve above is done; reuse it for M2's c'
-                cp_prev = cp;
-            }
-            double nxt = 0.0;
-            for (int j = N - 1; j >= 0; --j) {
-                nxt = y[j] - (j < N - 1 ? l[j] * nxt : 0.0);
-                y[j] = nxt;
-            }
+        if (numerov) {
+            // M2 t = y: forward t'_j = y_j/p_j - (1/12) t'_{j-1}/p_j, backward t_j = t'_j - (1/12)/p_j t_{j+1}
+            block_recurrence(y, mfa, N, false, sp, sv);
+            block_recurrence(y, mba, N, true, sp, sv);
         }
-        __syncthreads();
         double se = 0.0;
         for (int j = threadIdx.x; j < N; j += blockDim.x) se += psi[j] * (y[j] + V_at(j) * psi[j]);
         e = block_sum(se, red) * C.dx;
-        if (numerov) {
-            // restore the lower multipliers of A for the next iteration
-            for (int j = threadIdx.x; j < N; j += blockDim.x) l[j] = j == 0 ? 0.0 : A_lo(j);
-        }
         if (threadIdx.x == 0) stop = (it > 1 && fabs(e - e_prev) < tol) || it >= max_iter;
         __syncthreads();
         if (stop) break;
@@ -206,7 +244,8 @@ cudaError_t launch_ground_state(const ClassDesc* d_cls, int n_cls, int scheme, d
                                 double tol, double* d_work, const int64_t* d_work_off, double* d_energy,
                                 int64_t* d_iters, cudaStream_t st)
 {
-    k_ground_state<<<n_cls, 256, 0, st>>>(d_cls, scheme, dtau, max_iter, tol, d_work, d_work_off, d_energy, d_iters);
+    k_ground_state<<<n_cls, kGsThreads, 0, st>>>(d_cls, scheme, dtau, max_iter, tol, d_work, d_work_off, d_energy,
+                                                  d_iters);
     return cudaGetLastError();
 }
 
