@@ -23,7 +23,9 @@ constexpr int kMaxSegments = 16;    // warps per CTA at most (512 threads)
 //   nf[3j..3j+2] = the same three factors rounded to float2 (MIXED)
 //   fx[j]  = (x_j, dV_j, m_j, 0) rounded to float4 (MIXED observables and mask)
 //   vv[j]  = V_j                                                          (energy distribution)
-//   af[j]  = ab[j] rounded to float2                                      (FP64 path's float halo rows)
+//   af[j]  = ab[j] rounded to float2                                      (float halo rows)
+//   xff[j] = (x_j, dV_j) as float pairs (hi, lo), hi = x rounded to float, lo = x - hi rounded
+//            to float: a float4 (x_hi, x_lo, dV_hi, dV_lo)
 struct ClassDesc {
     int64_t tab_off;      // offset (in doubles) of the class block in the table buffer
     int32_t N;
@@ -61,7 +63,8 @@ __host__ __device__ inline int64_t tab_nf(const ClassDesc& c) { return c.tab_off
 __host__ __device__ inline int64_t tab_fx(const ClassDesc& c) { return c.tab_off + 14 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_vv(const ClassDesc& c) { return c.tab_off + 16 * (int64_t)c.N; }
 __host__ __device__ inline int64_t tab_af(const ClassDesc& c) { return c.tab_off + 17 * (int64_t)c.N; }
-inline int64_t tab_doubles(int N) { return 18 * (int64_t)N; }
+__host__ __device__ inline int64_t tab_xff(const ClassDesc& c) { return c.tab_off + 18 * (int64_t)c.N; }
+inline int64_t tab_doubles(int N) { return 20 * (int64_t)N; }
 
 // ---- host-side planning rules shared by the allocating and the static entry points ----
 

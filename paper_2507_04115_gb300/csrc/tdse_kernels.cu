@@ -58,6 +58,8 @@ __global__ void k_build_tables(const ClassDesc* cls, int n_cls, double dt, doubl
         }
         mk[j] = m;
         reinterpret_cast<float4*>(tab + tab_fx(C))[j] = make_float4((float)x, (float)dV, (float)m, 0.0f);
+        const float xh = (float)x, vh = (float)dV;
+        reinterpret_cast<float4*>(tab + tab_xff(C))[j] = make_float4(xh, (float)(x - (double)xh), vh, (float)(dV - (double)vh));
         tab[tab_vv(C) + j] = V;
     }
 }
