@@ -450,7 +450,6 @@ tdse_status build_plan(tdse_batch* b)
         const int P = b->class_P[G.cls], K = b->class_K[G.cls];
         G.P = P;
         G.K = K;
-        G.K2 = halo_double_rows(b->classes[G.cls].beta, K);
         G.m = group_segment_length(G.N, P, kLanes / G.I);
         // a sweep covers its segment and a halo on each side (m + 2K rows; the 32-wide propagation
         // clips it at the walls); a single exact segment covers the N points

@@ -48,8 +48,6 @@ struct GroupDesc {
     int32_t cls;          // class index
     int32_t N, P, K, m;   // grid size, warps carrying segments, halo, segment length
     int32_t I;            // instances per group (32, 16, 8, 4, 2 or 1)
-    int32_t K2;           // rows of each halo next to the segment that the FP64 path runs in double
-                          // (halo_double_rows); the outer K - K2 rows run in float
 };
 
 // Device-side tables offsets inside a class block (in doubles).
@@ -80,17 +78,6 @@ inline int halo_for_beta(double beta, double tol = 1e-18)
     if (b < 1e-3) return 8;
     const int K = (int)std::ceil(std::log(tol) / std::log(b));
     return std::max(K, 8);
-}
-
-// Rows of a halo that the FP64 path keeps in double, counted from the segment outwards: the outer
-// K - K2 rows run in float, and the error they leave (float rounding, ~1e-7 of the values) shrinks
-// by |gamma| <= beta per double row, so beta^K2 < 1e-11 brings it below 1e-18 like the truncation.
-inline int halo_double_rows(double beta, int K)
-{
-    if (K == 0) return 0;
-    const double b = std::fabs(beta);
-    const int K2 = b < 1e-3 ? 4 : (int)std::ceil(std::log(1e-11) / std::log(b));
-    return std::min(K, std::max(K2, 4));
 }
 
 // Segments of a class: at most the CTA's warps, and every segment at least four halos long

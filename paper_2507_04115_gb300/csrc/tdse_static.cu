@@ -49,7 +49,7 @@ tdse_status static_scratch(int dev, void** out)
 
 // Descriptors of a uniform batch written straight into the static scratch.
 __global__ void k_static_setup(ClassDesc C, int64_t n_inst, int64_t n_groups, int64_t nt, int64_t row_stride,
-                               int P, int K, int K2, int m, ClassDesc* cls, GroupDesc* groups, int64_t* slot_row,
+                               int P, int K, int m, ClassDesc* cls, GroupDesc* groups, int64_t* slot_row,
                                int64_t* slot_nt, int* status)
 {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,7 +64,6 @@ __global__ void k_static_setup(ClassDesc C, int64_t n_inst, int64_t n_groups, in
         G.N = C.N;
         G.P = P;
         G.K = K;
-        G.K2 = K2;
         G.m = m;
         G.I = kLanes;
         groups[g] = G;
@@ -185,8 +184,7 @@ extern "C" tdse_status tdse_propagate_static(const tdse_instance* inst_host, int
 
     cudaStream_t s = (cudaStream_t)stream;
     const int setup_blocks = (int)std::min<int64_t>(1024, (n_groups * kLanes + 255) / 256);
-    k_static_setup<<<setup_blocks, 256, 0, s>>>(C, n_inst, n_groups, n_steps, row_stride, P, K,
-                                                halo_double_rows(C.beta, K), m, d_cls, d_groups,
+    k_static_setup<<<setup_blocks, 256, 0, s>>>(C, n_inst, n_groups, n_steps, row_stride, P, K, m, d_cls, d_groups,
                                                 d_row, d_nt, d_status);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)

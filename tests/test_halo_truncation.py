@@ -118,15 +118,16 @@ def test_numerov_substitutions_with_exact_factors():
 
 
 def _halo_double_rows(beta, K):
-    # the planner's split of a halo: the rows nearest the segment in double, enough for an error of
-    # float rounding (1e-7 of the values) to shrink below 1e-18 (beta^K2 < 1e-11); the rest in float
+    # a split of a halo: the rows nearest the segment in double, enough for an error of float
+    # rounding (1e-7 of the values) to shrink below 1e-18 (beta^K2 < 1e-11); the rest in float
     return min(K, max(4, math.ceil(math.log(1e-11) / math.log(beta))))
 
 
 def _segment_solve_split(di, off, r, lo, hi, K, K2):
     """As _segment_solve, but the outer K - K2 rows of each halo run in float32 (complex64): the
     forward sweep from the top of the halo to K2 rows before the segment, and both sweeps over the
-    bottom halo's rows beyond K2 after the segment (the FP64 kernel's arithmetic split)."""
+    bottom halo's rows beyond K2 after the segment.  (The MIXED path runs its whole halo in float;
+    an FP64 variant with this split was measured slower than the all-double sweep and not kept.)"""
     N = di.size
     a, b = max(0, lo - K), min(N, hi + K)
     tf, bd = max(a, lo - K2), min(b, hi + K2)
