@@ -35,6 +35,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2507_04115_gb300.spectral_metrics import (FP64_BOUND, MIXED_BOUND, harmonic_cutoff,  # noqa: E402
+                                                    spectral_errors)
+
 METRIC = "1D-TDSE grid-point-steps/s (batched) & % pipe roofline; mixed vs FP64 at stated error"
 UNIT = "grid-point-steps/s"
 FLOPS_PER_POINT_STEP = 48.0          # algorithmic FULL_CN work per grid-point step (FMA = 2 flops)
@@ -158,27 +161,6 @@ def kernel_traffic_per_point_step():
         return float(kv["bytes_per_point_step"])
     except (KeyError, ValueError):
         return None
-
-
-def harmonic_cutoff(E0, omega, ip=0.579):
-    up = E0 ** 2 / (4 * omega ** 2)
-    return (ip + 3.17 * up) / omega
-
-
-def spectral_errors(S, S_ref, omega0, dt, L, q_cut):
-    """(i) relative L2 of S over bins with q <= 1.5 q_cut; (ii) max over odd harmonics q <= q_cut of
-    |S_q - S_q^ref| / S_q^ref with S_q the power integrated over +-omega0/2 around q omega0."""
-    k = np.arange(S.size)
-    q = k * 2 * np.pi / (L * dt) / omega0
-    sel = q <= 1.5 * q_cut
-    l2 = float(np.linalg.norm(S[sel] - S_ref[sel]) / np.linalg.norm(S_ref[sel]))
-    worst = 0.0
-    for h in range(1, int(q_cut) + 1, 2):
-        win = (q > h - 0.5) & (q <= h + 0.5)
-        if win.any():
-            a, b = S[win].sum(), S_ref[win].sum()
-            worst = max(worst, abs(a - b) / b)
-    return l2, worst
 
 
 def _oracle_job(args):
@@ -483,7 +465,7 @@ def own_arm(args):
             worst.append(w)
             series = max(series, float(np.max(np.abs(acc_host[i] - accs[j])) / np.max(np.abs(accs[j]))))
         spec_err = {"instances": len(sample_idx), "rel_l2_max": max(l2s), "harmonic_rel_max": max(worst),
-                    "a_series_rel_max": series, "q_cut": q_cut, "bound": 1e-6}
+                    "a_series_rel_max": series, "q_cut": q_cut, "bound": list(FP64_BOUND)}
 
     # mixed precision on the same workload: throughput over two chunks of the whole batch, and the
     # spectral error of the oracle sample propagated in full (one group, so it runs on one SM)
@@ -534,7 +516,8 @@ def own_arm(args):
                 l2, wv = spectral_errors(Sm[j], S_ref, omega, dt, L, q_cut)
                 l2s.append(l2)
                 worst.append(wv)
-            mixed["spectral_error"] = {"instances": k, "rel_l2_max": max(l2s), "harmonic_rel_max": max(worst)}
+            mixed["spectral_error"] = {"instances": k, "rel_l2_max": max(l2s), "harmonic_rel_max": max(worst),
+                                       "bound": list(MIXED_BOUND)}
 
     # the other configurations and rows, bounded so that the whole line stays within a few minutes
     secondary = None
@@ -1024,17 +1007,20 @@ def _oracle_pool(wl, idx, soft_of_inst):
     return pool, pool.map_async(_oracle_job, jobs, chunksize=1), cores
 
 
-def _fill_rows(torch, E, offs, wl, lo, hi, s0, S, dev):
-    """Field samples n = s0 .. s0 + S of instances [lo, hi) into E at offs (row i at offs[i] - offs[lo]),
-    on the device: E0 sin^2(pi t/Tp) cos(w (t - Tp/2) + phi) for t <= Tp, 0 after."""
-    cnt = hi - lo
-    t = (torch.arange(s0, s0 + S + 1, dtype=torch.float64, device=dev) * wl.dt)[None, :]
-    Tp = torch.as_tensor(wl.n_cycles[lo:hi] * 2 * np.pi / wl.omega[lo:hi], device=dev)[:, None]
-    w = torch.as_tensor(wl.omega[lo:hi], device=dev)[:, None]
-    e0 = torch.as_tensor(wl.E0[lo:hi], device=dev)[:, None]
-    ph = torch.as_tensor(wl.phi[lo:hi], device=dev)[:, None]
+def _pulse_params(torch, wl, dev):
+    """Per-instance pulse parameters as device columns (E0, omega, Tp, phi), made before any capture."""
+    return tuple(torch.as_tensor(v, dtype=torch.float64, device=dev)[:, None]
+                 for v in (wl.E0, wl.omega, wl.n_cycles * 2 * np.pi / wl.omega, wl.phi))
+
+
+def _fill_rows(torch, E, prm, dt, s0, S, dev):
+    """Field samples n = s0 .. s0 + S of every instance into E (rows of S + 1 samples), on the device:
+    E0 sin^2(pi t/Tp) cos(w (t - Tp/2) + phi) for t <= Tp, 0 after; prm from _pulse_params.  Device
+    work only, so it can be captured in a CUDA graph."""
+    e0, w, Tp, ph = prm
+    t = (torch.arange(s0, s0 + S + 1, dtype=torch.float64, device=dev) * dt)[None, :]
     env = torch.where(t <= Tp, torch.sin(np.pi * t / Tp) ** 2, torch.zeros_like(t))
-    E.view(cnt, S + 1).copy_(e0 * env * torch.cos(w * (t - 0.5 * Tp) + ph))
+    E.view(e0.shape[0], S + 1).copy_(e0 * env * torch.cos(w * (t - 0.5 * Tp) + ph))
 
 
 def _fill_full_rows(torch, E, offs, wl, dev, block=256):
@@ -1113,9 +1099,10 @@ def uneven_full(args, torch, tdse, inputs, softcore, dev):
         clocks = ClockSampler(0)
         clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        g.replay()
-        e1.record(st)
+        with torch.cuda.stream(st):            # replay() launches on the current stream
+            e0.record(st)
+            g.replay()
+            e1.record(st)
         torch.cuda.synchronize(dev)
         clk = clocks.stop()
         sec = e0.elapsed_time(e1) * 1e-3
@@ -1142,7 +1129,7 @@ def uneven_full(args, torch, tdse, inputs, softcore, dev):
                l2="fields, d and a resident: %.1f GB each" % (offs[-1] * 8 / 1e9)),
           dtype="f64", total_point_steps=pts, solves_per_s=n / out["fp64"]["seconds"],
           fp64=out["fp64"], mixed=dict(out["mixed"], speedup_vs_fp64=out["mixed"]["value"] / out["fp64"]["value"]),
-          gpu_launches=len(chunks) * 2, bound={"fp64": [1e-6, 1e-6], "mixed": [1e-3, 3e-2]},
+          gpu_launches=len(chunks) * 2, bound={"fp64": list(FP64_BOUND), "mixed": list(MIXED_BOUND)},
           cpu_baseline=out.get("cpu_baseline"))
 
 
@@ -1172,30 +1159,47 @@ def large_stream(args, torch, tdse, inputs, softcore, dev):
     ac = [torch.zeros_like(Ec[0]) for _ in range(2)]
     hb = [torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory() for _ in range(2)]
     sample_dev = torch.as_tensor(sample, device=dev)
+    prm = _pulse_params(torch, wl, dev)
     gathered = torch.zeros((n_timed, sample.size, S + 1), dtype=torch.float64, device=dev)
     if args.autotune:
-        _fill_rows(torch, Ec[0], offs, wl, 0, n, 0, S, dev)
+        _fill_rows(torch, Ec[0], prm, dt, 0, S, dev)
         b.autotune(Ec[0], dc[0], ac[0], 0, min(S, args.tune_steps), sample_base=0)
         b.ground_state()
     plan = b.plan()
     main = torch.cuda.current_stream(dev)
     for c in range(n_warm):                     # eager warm-up chunks (the first steps of the pulse)
-        _fill_rows(torch, Ec[c % 2], offs, wl, 0, n, c * S, S, dev)
+        _fill_rows(torch, Ec[c % 2], prm, dt, c * S, S, dev)
         b.propagate(Ec[c % 2], dc[c % 2], ac[c % 2], c * S, (c + 1) * S, sample_base=c * S)
         hb[c % 2].copy_(ac[c % 2], non_blocking=True)
     torch.cuda.synchronize(dev)
     st, cs = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     st.wait_stream(main)
-    g = torch.cuda.CUDAGraph()
+    # one captured graph per timed chunk (field synthesis on the device and the persistent launch),
+    # sharing one memory pool; the copy-back is not captured: it runs on the copy stream between
+    # the replays, double-buffered (chunk c + 2 reuses chunk c's buffers once its copy is done)
+    graphs = []
+    pool = None
+    for k in range(n_timed):
+        c = n_warm + k
+        s0 = c * S
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st, pool=pool):
+            _fill_rows(torch, Ec[c % 2], prm, dt, s0, S, dev)
+            b.propagate(Ec[c % 2], dc[c % 2], ac[c % 2], s0, s0 + S, sample_base=s0, stream=st)
+        pool = g.pool()
+        graphs.append(g)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     copy_done = {}
-    with torch.cuda.graph(g, stream=st):
-        for k in range(n_timed):
+    with torch.cuda.stream(st):
+        e0.record(st)
+        for k, g in enumerate(graphs):
             c = n_warm + k
-            s0, s1 = c * S, (c + 1) * S
-            if c - 2 in copy_done:              # buffer c % 2 is free once chunk c - 2's copy is done
+            if c - 2 in copy_done:
                 st.wait_event(copy_done[c - 2])
-            _fill_rows(torch, Ec[c % 2], offs, wl, 0, n, s0, S, dev)
-            b.propagate(Ec[c % 2], dc[c % 2], ac[c % 2], s0, s1, sample_base=s0, stream=st)
+            g.replay()
             done = torch.cuda.Event()
             done.record(st)
             cs.wait_event(done)
@@ -1206,12 +1210,7 @@ def large_stream(args, torch, tdse, inputs, softcore, dev):
                 ev.record(cs)
             copy_done[c] = ev
         st.wait_stream(cs)
-    clocks = ClockSampler(0)
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    g.replay()
-    e1.record(st)
+        e1.record(st)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     sec = e0.elapsed_time(e1) * 1e-3
@@ -1244,13 +1243,13 @@ def large_stream(args, torch, tdse, inputs, softcore, dev):
     _line(METRIC, timed_pts / sec, UNIT, args, wl.name,
           dict(instances=n, N=N, Nt=Nt, chunk_steps=S, warmup_chunks=n_warm, timed_chunks=n_timed,
                timed_fraction_of_pulse=n_timed * S / Nt, precision="mixed",
-               pipeline="per chunk: field synthesised on the device, tdse_propagate, a(t) chunk copied to "
-                        "double-buffered pinned host memory on a second stream overlapping the next chunk; "
-                        "the timed chunks captured once in a CUDA graph and replayed",
+               pipeline="per chunk: a captured CUDA graph (field synthesised on the device, tdse_propagate) "
+                        "replayed on the compute stream, then the a(t) chunk copied to double-buffered pinned "
+                        "host memory on a second stream while the next chunk's graph runs",
                launch=dict((k, plan[k]) for k in ("warps_per_cta", "ctas", "slice_steps", "segments", "halo"))),
           dtype="f32 psi / f64 elimination and sums", clocks=clk, nonfinite_instance=bad,
           total_point_steps=wl.point_steps(), d2h_bytes_per_chunk=int(offs[-1]) * 8,
-          sample_matches_large_batch_bitwise=bool(same), spectral_error=spec, bound=[1e-3, 3e-2],
+          sample_matches_large_batch_bitwise=bool(same), spectral_error=spec, bound=list(MIXED_BOUND),
           gpu_launches=n_timed)
 
 

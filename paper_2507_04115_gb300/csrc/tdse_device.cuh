@@ -45,6 +45,64 @@ struct Fma64 {
     __device__ __forceinline__ float mul(float x, float y) const { return x * y; }
 };
 
+// ---- float pairs on the FP32 pipe (no FP64 instruction; GB300 runs FP32 at 64x its FP64 rate) ----
+
+// v >= 0 (a squared modulus) as h + l with h, l floats: h its leading 24 significant bits, l the rest
+// truncated to 24 bits, so |h + l - v| < 2^-47 v + 2^-126 (parts below float's normal range flush
+// to zero).  Integer operations on the double's two words only.  Infinity and NaN map to a float infinity or NaN; values beyond float's range to infinity,
+// so a non-finite state still shows in the sums.
+__device__ __forceinline__ void split_ff(double v, float& h, float& l)
+{
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    unsigned hb = ((e - 896u) << 23) | (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    hb = e < 897u ? 0u : hb;
+    const bool special = e > 1150u;   // beyond float's range, infinity or NaN
+    const bool nan = e == 2047u && ((((unsigned)hi & 0xfffffu) | lo) != 0u);
+    hb = special ? (nan ? 0x7fc00000u : 0x7f800000u) : hb;
+    h = __uint_as_float(hb);
+    const unsigned m29 = lo & 0x1fffffffu;
+    const int lz = __clz(m29);
+    const unsigned long long t = ((unsigned long long)m29 << (lz + 1)) & 0xffffffffull;
+    const int fe = (int)e - 917 - lz;
+    unsigned lb = ((unsigned)fe << 23) | (unsigned)(t >> 9);
+    lb = (m29 == 0u || fe <= 0 || e < 897u || special) ? 0u : lb;
+    l = __uint_as_float(lb);
+}
+
+// float -> double by integer operations (exact for normal floats and infinities/NaN; zero and
+// subnormals give a signed zero)
+__device__ __forceinline__ double f2d_int(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned sign = b & 0x80000000u;
+    unsigned h = sign | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    h = e == 255u ? (sign | 0x7ff00000u | ((b & 0x7fffffu) >> 3) | ((b & 0x7fffffu) ? 0x80000u : 0u)) : h;
+    const unsigned l = e == 255u ? 0u : b << 29;
+    return e == 0u ? __hiloint2double((int)sign, 0) : __hiloint2double((int)h, (int)l);
+}
+
+// (sh, sl) += (ah, al): exact two-sum of the leading parts, rounding errors and low parts into sl
+__device__ __forceinline__ void ff_acc(float& sh, float& sl, float ah, float al)
+{
+    const float t = sh + ah;
+    const float bp = t - sh;
+    const float err = (sh - (t - bp)) + (ah - bp);
+    sl += err + al;
+    sh = t;
+}
+
+// (sh, sl) += (xh + xl)(rh + rl): the leading product exact by an FMA, the cross terms in float
+// (the xl rl term, ~2^-48 of the product, is dropped)
+__device__ __forceinline__ void ff_fma_acc(float& sh, float& sl, float xh, float xl, float rh, float rl)
+{
+    const float p = xh * rh;
+    const float e = fmaf(xh, rh, -p);
+    ff_acc(sh, sl, p, fmaf(xh, rl, fmaf(xl, rh, e)));
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll

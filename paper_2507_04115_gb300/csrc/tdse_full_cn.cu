@@ -507,10 +507,10 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                             fn += rho;
                             fx = fma(fxv.x, rho, fx);
                             fv = fma(fxv.y, rho, fv);
-                            if (++blk == 8) {
-                                o.n += (double)fn;
-                                o.x += (double)fx;
-                                o.v += (double)fv;
+                            if (++blk == kObsBlock) {
+                                o.n = F.add(f2d_int(fn), o.n);
+                                o.x = F.add(f2d_int(fx), o.x);
+                                o.v = F.add(f2d_int(fv), o.v);
                                 fn = fx = fv = 0;
                                 blk = 0;
                             }
@@ -525,9 +525,9 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                         issued = b + kRing + 1;
                     }
                 }
-                o.n += (double)fn;
-                o.x += (double)fx;
-                o.v += (double)fv;
+                o.n = F.add(f2d_int(fn), o.n);
+                o.x = F.add(f2d_int(fx), o.x);
+                o.v = F.add(f2d_int(fv), o.v);
                 rc += (uint32_t)max(nblk, 0);
             } else {
                 const Cx* r = sc + (int64_t)(hi - 1 - lo) * (2 * kLanes);
@@ -545,7 +545,13 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 Cx* pw = ps + (int64_t)(e - 1) * kLanes + lane;       // psi_j (store)
                 const Cx* pl = pw - 2 * kLanes;                        // psi_{j-2} (prefetch)
                 const double* tm = tab_m + (e - 1);
-                const double2* txv = tab_xv2 + (e - 1);
+                const float4* txf = reinterpret_cast<const float4*>(tab + tab_xff(C)) + (e - 1);
+                // observable sums: rho = |psi|^2 in double, split into a float pair, summed as float
+                // pairs over blocks of kObsBlock points on the FP32 pipe (with x and dV/dx as float
+                // pairs), each block's pair widened to double (integer operations) and added in
+                // double: 2 FP64 instructions per block and sum instead of 1 per point and sum
+                float snh = 0.f, snl = 0.f, sxh = 0.f, sxl = 0.f, svh = 0.f, svl = 0.f;
+                int blk = 0;
                 if (e - 1 >= s) {
                     ga = r[lane];
                     da = r[kLanes + lane];
@@ -582,13 +588,25 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     --tm;
                     if (active) *pw = mk(xr, xi);
                     pw -= kLanes;
-                    const R rho = fma(xr, xr, F.mul(xi, xi));
-                    const double2 xv = __ldg(txv);
-                    --txv;
-                    o.n = F.add(rho, o.n);
-                    o.x = fma(xv.x, rho, o.x);
-                    o.v = fma(xv.y, rho, o.v);
+                    const double rho = fma(xr, xr, F.mul(xi, xi));
+                    float rh, rl;
+                    split_ff(rho, rh, rl);
+                    const float4 xf = __ldg(txf);
+                    --txf;
+                    ff_acc(snh, snl, rh, rl);
+                    ff_fma_acc(sxh, sxl, xf.x, xf.y, rh, rl);
+                    ff_fma_acc(svh, svl, xf.z, xf.w, rh, rl);
+                    if (++blk == kObsBlock) {
+                        o.n = F.add(f2d_int(snh), F.add(f2d_int(snl), o.n));
+                        o.x = F.add(f2d_int(sxh), F.add(f2d_int(sxl), o.x));
+                        o.v = F.add(f2d_int(svh), F.add(f2d_int(svl), o.v));
+                        snh = snl = sxh = sxl = svh = svl = 0.f;
+                        blk = 0;
+                    }
                 }
+                o.n = F.add(f2d_int(snh), F.add(f2d_int(snl), o.n));
+                o.x = F.add(f2d_int(sxh), F.add(f2d_int(sxl), o.x));
+                o.v = F.add(f2d_int(svh), F.add(f2d_int(svl), o.v));
             }
             const ObsSums t = reduce_obs(o, red, P);   // its barrier also orders this step's psi writes
             if (w == 0 && active) {

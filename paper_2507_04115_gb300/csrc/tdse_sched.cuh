@@ -13,6 +13,9 @@ namespace tdse {
 // SM let the FP64-heavy forward sweep of one group overlap the float back substitution of another
 // (each CTA synchronises only its own warps).
 constexpr int kSlotRows = 8;
+// Points per block of the observable sums kept on the FP32 pipe before a block is added in double
+// (FP64 path: float-pair sums; MIXED: float sums of the float state).
+constexpr int kObsBlock = 16;
 constexpr int kSlotBytes = kSlotRows * 768;
 constexpr int kMaxRing = 4;
 constexpr int kMinRing = 2;

@@ -1,34 +1,11 @@
-"""The spectral-error metric of the stated bounds (reading Err): two numbers against the FP64
-oracle's spectrum S_ref of the same instance,
-  (i)  relative L2 of S over the bins with q <= 1.5 q_cut,
-  (ii) max over the odd harmonics h <= q_cut of |S_h - S_h^ref| / S_h^ref, S_h the power summed
-       over the bins with h - 1/2 < q <= h + 1/2,
-with q = omega / omega0 and q_cut = (I_p + 3.17 U_p) / omega0, U_p = E0^2 / (4 omega0^2) (Sec. 7.1's
-cutoff law, I_p = 0.579 a.u.)."""
-import numpy as np
+"""Test helpers for the spectral comparisons: the metric and the stated bounds (from the package's
+spectral_metrics) and the oracle propagations in spawned worker processes."""
+import os
+import sys
 
-# Stated bounds of the two precisions (the same pair is quoted in the design notes and the benchmark)
-FP64_BOUND = (1e-6, 1e-6)
-MIXED_BOUND = (1e-3, 3e-2)
-
-
-def harmonic_cutoff(E0, omega, ip=0.579):
-    up = E0 ** 2 / (4 * omega ** 2)
-    return (ip + 3.17 * up) / omega
-
-
-def spectral_errors(S, S_ref, omega0, dt, L, q_cut):
-    k = np.arange(S.size)
-    q = k * 2 * np.pi / (L * dt) / omega0
-    sel = q <= 1.5 * q_cut
-    l2 = float(np.linalg.norm(S[sel] - S_ref[sel]) / np.linalg.norm(S_ref[sel]))
-    worst = 0.0
-    for h in range(1, int(q_cut) + 1, 2):
-        win = (q > h - 0.5) & (q <= h + 0.5)
-        if win.any():
-            a, b = S[win].sum(), S_ref[win].sum()
-            worst = max(worst, abs(a - b) / b)
-    return l2, worst
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+from paper_2507_04115_gb300.spectral_metrics import (FP64_BOUND, MIXED_BOUND, harmonic_cutoff,  # noqa: E402,F401
+                                                    spectral_errors)
 
 
 def oracle_job(args):

@@ -1,0 +1,75 @@
+"""The integer float-pair split and widening the propagation kernels use for their observable sums
+(no GPU): a numpy restatement of the bit operations on the double's and the float's words, checked
+against the bounds their comments state, |h + l - v| < 2^-47 v + 2^-126 for the split of v >= 0 and
+exactness of the widening, with infinities and NaN carried through."""
+import numpy as np
+
+
+def _split(v):
+    b = np.asarray(v, dtype=np.float64).view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.int64)
+    lo = (b & np.uint64(0xffffffff)).astype(np.int64)
+    e = (hi >> 20) & 0x7ff
+    hb = ((e - 896) << 23) | ((hi & 0xfffff) << 3) | (lo >> 29)
+    hb = np.where(e < 897, 0, hb)
+    special = e > 1150
+    nan = (e == 2047) & (((hi & 0xfffff) | lo) != 0)
+    hb = np.where(special, np.where(nan, 0x7fc00000, 0x7f800000), hb)
+    m29 = lo & 0x1fffffff
+    lz = np.where(m29 == 0, 32, 31 - np.floor(np.log2(np.maximum(m29, 1))).astype(np.int64))
+    t = (m29 << (lz + 1)) & 0xffffffff
+    fe = e - 917 - lz
+    lb = (fe << 23) | (t >> 9)
+    lb = np.where((m29 == 0) | (fe <= 0) | (e < 897) | special, 0, lb)
+    h = (hb & 0xffffffff).astype(np.uint32).view(np.float32)
+    l = (lb & 0xffffffff).astype(np.uint32).view(np.float32)
+    return h, l
+
+
+def _widen(f):
+    b = np.asarray(f, dtype=np.float32).view(np.uint32).astype(np.int64)
+    e = (b >> 23) & 0xff
+    sign = b & 0x80000000
+    m = b & 0x7fffff
+    h = sign | ((e + 896) << 20) | (m >> 3)
+    h = np.where(e == 255, sign | 0x7ff00000 | (m >> 3) | np.where(m != 0, 0x80000, 0), h)
+    l = np.where(e == 255, 0, (b << 29) & 0xffffffff)
+    h = np.where(e == 0, sign, h)
+    l = np.where(e == 0, 0, l)
+    return ((h.astype(np.uint64) << np.uint64(32)) | l.astype(np.uint64)).view(np.float64)
+
+
+def test_split_bound_over_the_whole_range():
+    rng = np.random.default_rng(17)
+    v = np.concatenate([
+        np.exp(rng.uniform(np.log(1e-40), np.log(3e38), 200000)),
+        rng.uniform(0.0, 1.0, 50000) ** 8,
+        [0.0, 1.0, 2.0 ** -126, 2.0 ** -127, 2.0 ** -149, np.nextafter(1.0, 2.0), 3.4e38, 2.0 ** 127 * (2 - 2.0 ** -40)],
+    ])
+    h, l = _split(v)
+    assert np.all(np.isfinite(h)) and np.all(np.isfinite(l)) and np.all(l >= 0)
+    # h exact as the leading bits: the split is exact where the remaining bits fit
+    err = np.abs(h.astype(np.float64) + l.astype(np.float64) - v)
+    assert np.all(err < 2.0 ** -47 * v + 2.0 ** -126)
+    # the bound is nearly reached (so a split that dropped l would fail)
+    assert np.max(err[v > 1e-30] / v[v > 1e-30]) > 2.0 ** -50
+    h0, _ = _split(v[v > 1e-30])
+    assert np.max(np.abs(h0.astype(np.float64) - v[v > 1e-30]) / v[v > 1e-30]) > 2.0 ** -26
+
+
+def test_split_carries_infinity_and_nan():
+    h, l = _split(np.array([np.inf, np.nan, 1e300, 3.5e38]))
+    assert np.isinf(h[0]) and np.isnan(h[1]) and np.isinf(h[2]) and np.isinf(h[3])
+    assert np.all(l == 0)
+
+
+def test_widening_is_exact():
+    rng = np.random.default_rng(18)
+    f = np.concatenate([
+        (rng.standard_normal(100000) * np.exp(rng.uniform(-80, 80, 100000))).astype(np.float32),
+        np.array([0.0, -0.0, 1.0, -2.5, np.float32(1.1754944e-38), np.float32(3.4028235e38)], dtype=np.float32),
+    ])
+    w = _widen(f)
+    assert np.array_equal(w, f.astype(np.float64))
+    s = _widen(np.array([np.inf, -np.inf, np.nan, np.float32(1e-40)], dtype=np.float32))
+    assert s[0] == np.inf and s[1] == -np.inf and np.isnan(s[2]) and s[3] == 0.0
