@@ -36,7 +36,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_2507_04115_gb300.spectral_metrics import (FP64_BOUND, MIXED_BOUND, harmonic_cutoff,  # noqa: E402
-                                                    spectral_errors)
+                                                    plateau_errors_by_decades, spectral_errors)
 
 METRIC = "1D-TDSE grid-point-steps/s (batched) & % pipe roofline; mixed vs FP64 at stated error"
 UNIT = "grid-point-steps/s"
@@ -844,7 +844,8 @@ def other_workload(args):
         return
 
     if args.workload == "adjoint":
-        r = measure_adjoint(torch, tdse, inputs, softcore, dev, stream, args.nt, args.autotune, args.tune_steps)
+        r = measure_adjoint(torch, tdse, inputs, softcore, dev, stream, args.nt, args.autotune, args.tune_steps,
+                            n_inst=args.instances if args.instances < 1024 else 0)
         cfg = r.pop("config")
         _line("1D-TDSE adjoint gradient, forward-equivalent grid-point-steps/s", r.pop("value"), UNIT, args,
               r.pop("workload"), cfg, dtype="f64", **r)
@@ -919,20 +920,23 @@ def measure_numerov(torch, tdse, inputs, softcore, dev, stream, steps=300, autot
     return out
 
 
-def measure_adjoint(torch, tdse, inputs, softcore, dev, stream, nt=0, autotune=1, tune_steps=256, plain=True):
+def measure_adjoint(torch, tdse, inputs, softcore, dev, stream, nt=0, autotune=1, tune_steps=256, plain=True,
+                    n_inst=0):
     """The adjoint batch (1024 x 2048, 6 cycles): the forward propagation, the checkpointed forward
     (recording a checkpoint every 256 steps) and the adjoint gradient of the harmonic 21-31 yield
     from those checkpoints, each timed once; with `plain`, also tdse_adjoint, which runs its own
-    forward pass."""
+    forward pass.  n_inst > 0 takes the first n_inst instances only, laid out as in the whole
+    batch (4 lanes per instance): a profiling case with fewer groups and tapes."""
     wl = inputs.adjoint_batch()
-    n = wl.n_inst
+    n = wl.n_inst if n_inst <= 0 else min(n_inst, wl.n_inst)
     N, dx, dt = int(wl.N[0]), float(wl.dx[0]), wl.dt
     Nt = int(wl.n_steps[0]) if nt <= 0 else nt
     a = softcore.fit_softening(wl.target_energy, N, dx)
     E = torch.empty((n, Nt + 1), dtype=torch.float64, device=dev)
-    inputs.sin2_pulse_batch(Nt, dt, wl.E0, float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi, out=E, xp=torch)
+    inputs.sin2_pulse_batch(Nt, dt, wl.E0[:n], float(wl.omega[0]), float(wl.n_cycles[0]), wl.phi[:n], out=E, xp=torch)
     E = E.reshape(-1).contiguous()
-    b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent))
+    b = tdse.Batch([N] * n, dx, a, [Nt] * n, dt, absorber=(wl.mask_width, wl.mask_exponent),
+                   lanes_per_instance=4 if n < wl.n_inst else 0)
     b.ground_state()
     d, acc = torch.zeros_like(E), torch.zeros_like(E)
     if autotune:
@@ -1043,24 +1047,30 @@ def _sample_errors(tdse, wl, idx, rows_gpu, refs, dev):
     a(t) rows against the oracle's; the GPU spectra come from tdse_spectrum."""
     import oracle
     import torch
-    l2s, hs = [], []
+    l2s, hs, byd = [], [], {}
     for j, i in enumerate(idx):
         a_row = rows_gpu[j]
         L = a_row.numel()
         S = tdse.spectrum(a_row.to(dev).contiguous(), [0, L], wl.dt, 0, L).cpu().numpy()[0]
         S_ref = oracle.spectrum(refs[j], wl.dt)
         omega = float(wl.omega[i])
-        l2, h = spectral_errors(S, S_ref, omega, wl.dt, L, harmonic_cutoff(float(wl.E0[i]), omega))
+        qc = harmonic_cutoff(float(wl.E0[i]), omega)
+        l2, h = spectral_errors(S, S_ref, omega, wl.dt, L, qc)
         l2s.append(l2)
         hs.append(h)
-    return {"instances": len(idx), "rel_l2_max": max(l2s), "harmonic_rel_max": max(hs)}
+        for D, e in plateau_errors_by_decades(S, S_ref, omega, wl.dt, L, qc).items():
+            byd[D] = max(byd.get(D, 0.0), e)
+    return {"instances": len(idx), "rel_l2_max": max(l2s), "harmonic_rel_max": max(hs),
+            "plateau_harmonic_rel_max_within_decades": byd}
 
 
 def uneven_full(args, torch, tdse, inputs, softcore, dev):
     """The uneven batch (16384 instances, N 1024..8192, up to 198575 steps) through the whole pulse
-    of every instance, FP64 then MIXED: fields resident on the device, one persistent launch per
-    chunk of steps, the chunk sequence captured once in a CUDA graph and replayed (timed); spectral
-    error of the oracle sample (64 instances, seed 102) on the run's own a(t)."""
+    of every instance, FP64 then MIXED: fields resident on the device, one persistent launch over
+    every step of every instance (or one per chunk of --nt steps), captured once in a CUDA graph and
+    replayed (timed); spectral error of the oracle sample (64 instances, seed 102) on the run's own
+    a(t).  One launch lets the scheduler run the longest groups from the start (a launch per chunk
+    waits at every chunk's end for its longest group)."""
     wl = inputs.uneven_batch()
     n = wl.n_inst
     classes = sorted(set(zip(wl.N.tolist(), wl.dx.tolist())))
@@ -1076,7 +1086,7 @@ def uneven_full(args, torch, tdse, inputs, softcore, dev):
         pool, res, cores = _oracle_pool(wl, sample, a)
     E = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
     _fill_full_rows(torch, E, offs, wl, dev)
-    S = int(args.nt) if args.nt > 0 else 20000
+    S = int(args.nt) if args.nt > 0 else Nt_max   # default: the whole job in one persistent launch
     chunks = [(s0, min(Nt_max, s0 + S)) for s0 in range(0, Nt_max, S)]
     pts = wl.point_steps()
     out, rows = {}, {}
@@ -1125,11 +1135,11 @@ def uneven_full(args, torch, tdse, inputs, softcore, dev):
     _line(METRIC, out["fp64"]["value"], UNIT, args, wl.name,
           dict(instances=n, classes=len(classes), Nt_max=Nt_max, chunk_steps=S, chunks=len(chunks),
                steps_covered="every step of every instance", precision="fp64 (mixed in 'mixed')",
-               graph="the chunk sequence captured once in a CUDA graph and replayed",
+               graph="the launch sequence captured once in a CUDA graph and replayed",
                l2="fields, d and a resident: %.1f GB each" % (offs[-1] * 8 / 1e9)),
           dtype="f64", total_point_steps=pts, solves_per_s=n / out["fp64"]["seconds"],
           fp64=out["fp64"], mixed=dict(out["mixed"], speedup_vs_fp64=out["mixed"]["value"] / out["fp64"]["value"]),
-          gpu_launches=len(chunks) * 2, bound={"fp64": list(FP64_BOUND), "mixed": list(MIXED_BOUND)},
+          gpu_launches=len(chunks), bound={"fp64": list(FP64_BOUND), "mixed": list(MIXED_BOUND)},
           cpu_baseline=out.get("cpu_baseline"))
 
 
@@ -1178,15 +1188,15 @@ def large_stream(args, torch, tdse, inputs, softcore, dev):
     # sharing one memory pool; the copy-back is not captured: it runs on the copy stream between
     # the replays, double-buffered (chunk c + 2 reuses chunk c's buffers once its copy is done)
     graphs = []
-    pool = None
+    gpool = None
     for k in range(n_timed):
         c = n_warm + k
         s0 = c * S
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=st, pool=pool):
+        with torch.cuda.graph(g, stream=st, pool=gpool):
             _fill_rows(torch, Ec[c % 2], prm, dt, s0, S, dev)
             b.propagate(Ec[c % 2], dc[c % 2], ac[c % 2], s0, s0 + S, sample_base=s0, stream=st)
-        pool = g.pool()
+        gpool = g.pool()
         graphs.append(g)
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(0)
@@ -1220,9 +1230,11 @@ def large_stream(args, torch, tdse, inputs, softcore, dev):
     # the oracle sample through the whole pulse with the large batch's layout (32-wide groups, same
     # warps and slice): the same arithmetic per instance as inside the large batch
     k_s = sample.size
-    rows = wl.field_rows(sample)
-    so = np.concatenate([[0], np.cumsum([r.size for r in rows])])
-    Es = torch.from_numpy(np.concatenate(rows)).to(dev)
+    # the same device synthesis as the chunks (bit-identical samples): whole rows of Nt + 1 samples
+    so = np.arange(k_s + 1, dtype=np.int64) * (Nt + 1)
+    Es = torch.empty(int(so[-1]), dtype=torch.float64, device=dev)
+    sd = torch.as_tensor(sample, device=dev)
+    _fill_rows(torch, Es, tuple(p.index_select(0, sd) for p in prm), dt, 0, Nt, dev)
     bs = tdse.Batch(wl.N[sample], wl.dx[sample], a_soft, wl.n_steps[sample], dt, row_offsets=so,
                     absorber=(wl.mask_width, wl.mask_exponent), precision=tdse.TDSE_MIXED, lanes_per_instance=1)
     bs.set_launch(plan["warps_per_cta"], 1, plan["slice_steps"])

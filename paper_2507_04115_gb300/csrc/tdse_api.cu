@@ -274,13 +274,12 @@ int default_warps(const tdse_batch* b)
     return 8;
 }
 
-// Lanes per instance for the lane-split layout, from a cost model of one time step: a group's
-// step costs ceil(P/4) x (27 m + 36 K) FP64 warp instructions on its busiest SM sub-partition
-// (27 per own point: forward elimination 16, back substitution and update 11; 36 per halo point:
-// 2K forward rows and K back-substitution rows), with m = N / (P L).  The step time is the larger
-// of (total work / SMs) and the longest single group (one group runs on one SM).  L = 1 keeps
-// 32 instances per warp; a larger L is taken only when it is clearly faster, i.e. when the
-// batch has too few groups to occupy the SMs.  Classes without a usable halo keep L = 1.
+// Lanes per instance for the lane-split layout, from the cost model of one time step
+// (group_step_cost): the step time is the larger of (total work / SMs) and the longest single
+// group (one group runs on one SM).  L = 1 keeps 32 instances per warp; a larger L is taken only
+// when it is clearly faster, i.e. when the batch has too few groups to occupy the SMs.  Classes
+// without a usable halo keep L = 1.  build_groups then widens single groups further where the
+// whole job's makespan asks for it (plan_widths).
 // Decay rate per point of a class's truncated sweeps: |gamma| <= beta for FULL_CN, max(|L|, |C|)
 // of the factors for NUMEROV_SPLIT.
 double class_decay(const tdse_batch* b, const ClassDesc& C)
@@ -307,9 +306,7 @@ int model_lanes(const tdse_batch* b, const std::vector<int64_t>& class_count)
             const ClassDesc& C = b->classes[c];
             const int K = class_halo(b, C);
             const int Lc = K == 0 ? 1 : L;
-            const int P = Lc == 1 ? class_segments(C.N, K, warps) : std::max(1, std::min(warps, C.N / Lc));
-            const int m = group_segment_length(C.N, P, Lc);
-            const double cost = std::ceil(P / 4.0) * (27.0 * m + 36.0 * (P * Lc > 1 ? K : 0));
+            const double cost = group_step_cost(C.N, K, Lc, warps);
             const double groups = std::ceil((double)class_count[c] * Lc / kLanes);
             work += groups * cost;
             longest = std::max(longest, cost);
@@ -324,7 +321,10 @@ int model_lanes(const tdse_batch* b, const std::vector<int64_t>& class_count)
 }
 
 // Slots and groups: instances ordered by class, then by decreasing Nt (long groups first), cut
-// into groups of I = 32/L; (re)allocates everything sized by the grouping.  The state is lost.
+// into groups of I = 32/L instances, L per group: the per-step model's L (model_lanes) or the
+// caller's (tdse_set_layout) for every group, widened for the longest groups where the makespan
+// estimate asks for it (plan_widths; not under tdse_set_layout).  (Re)allocates everything sized by
+// the grouping.  The state is lost.
 tdse_status build_groups(tdse_batch* b)
 {
     const int n_cls = (int)b->classes.size();
@@ -332,8 +332,6 @@ tdse_status build_groups(tdse_batch* b)
     std::vector<int64_t> class_count(n_cls, 0);
     for (int64_t i = 0; i < n_inst; ++i) ++class_count[b->inst_class[i]];
     const int L = b->lanes_request > 0 ? b->lanes_request : model_lanes(b, class_count);
-    b->class_L.assign(n_cls, 1);
-    for (int c = 0; c < n_cls; ++c) b->class_L[c] = class_halo(b, b->classes[c]) == 0 ? 1 : L;
 
     std::vector<int64_t> order(n_inst);
     for (int64_t i = 0; i < n_inst; ++i) order[i] = i;
@@ -341,6 +339,22 @@ tdse_status build_groups(tdse_batch* b)
         if (b->inst_class[p] != b->inst_class[q]) return b->inst_class[p] < b->inst_class[q];
         return b->n_steps[p] > b->n_steps[q];
     });
+    const int warps = b->warps_override > 0 ? b->warps_override : default_warps(b);
+    std::vector<WidthClass> wc(n_cls);
+    for (int c = 0; c < n_cls; ++c) {
+        wc[c].N = b->classes[c].N;
+        wc[c].K = class_halo(b, b->classes[c]);
+        wc[c].L_base = wc[c].K == 0 ? 1 : L;
+    }
+    for (int64_t k = 0; k < n_inst; ++k) wc[b->inst_class[order[k]]].nt_desc.push_back(b->n_steps[order[k]]);
+    std::vector<std::vector<int>> widths;
+    if (b->lanes_request > 0)
+        plan_widths_at(wc, warps, b->sm_count, std::numeric_limits<double>::infinity(), &widths);
+    else
+        plan_widths(wc, warps, b->sm_count, &widths);
+    b->class_L.assign(n_cls, 1);
+    for (int c = 0; c < n_cls; ++c)
+        for (int Lg : widths[c]) b->class_L[c] = std::max(b->class_L[c], Lg);
     b->groups.clear();
     b->slot_group.clear();
     b->slot_of_inst.assign(n_inst, -1);
@@ -348,8 +362,10 @@ tdse_status build_groups(tdse_batch* b)
     int64_t psi_elems = 0;
     for (int64_t k = 0; k < n_inst;) {
         const int c = b->inst_class[order[k]];
-        const int I = kLanes / b->class_L[c];
+        size_t gk = 0;   // group index within the class
         while (k < n_inst && b->inst_class[order[k]] == c) {
+            const int I = kLanes / (gk < widths[c].size() ? widths[c][gk] : widths[c].back());
+            ++gk;
             GroupDesc G{};
             G.cls = c;
             G.N = b->classes[c].N;
@@ -435,22 +451,19 @@ tdse_status build_plan(tdse_batch* b)
     b->slice = b->slice_override > 0 ? b->slice_override : 16;
     b->class_P.assign(n_cls, 1);
     b->class_K.assign(n_cls, 0);
-    for (int c = 0; c < n_cls; ++c) {
-        const ClassDesc& C = b->classes[c];
-        int K = class_halo(b, C);
-        const int L = b->class_L[c];
-        // lane-split classes use every warp (short segments are the price of filling the GPU)
-        const int P = L == 1 ? class_segments(C.N, K, b->warps) : std::max(1, std::min(b->warps, C.N / L));
-        if (P == 1 && L == 1) K = 0;
-        b->class_P[c] = P;
-        b->class_K[c] = K;
-    }
     int rows = 1;
     for (auto& G : b->groups) {
-        const int P = b->class_P[G.cls], K = b->class_K[G.cls];
+        const ClassDesc& C = b->classes[G.cls];
+        const int L = kLanes / G.I;
+        int K = class_halo(b, C);
+        const int P = group_warps(C.N, K, L, b->warps);
+        if (P == 1 && L == 1) K = 0;   // one exact segment
         G.P = P;
         G.K = K;
-        G.m = group_segment_length(G.N, P, kLanes / G.I);
+        G.m = group_segment_length(G.N, P, L);
+        G.w = std::max(1, (int)std::lround(group_step_cost(C.N, K, L, b->warps) / 64.0));
+        b->class_P[G.cls] = std::max(b->class_P[G.cls], P);
+        b->class_K[G.cls] = std::max(b->class_K[G.cls], K);
         // a sweep covers its segment and a halo on each side (m + 2K rows; the 32-wide propagation
         // clips it at the walls); a single exact segment covers the N points
         rows = std::max(rows, P * (kLanes / G.I) == 1 ? G.N : G.m + 2 * K);

@@ -84,21 +84,25 @@ __device__ __forceinline__ double f2d_int(float f)
     return e == 0u ? __hiloint2double((int)sign, 0) : __hiloint2double((int)h, (int)l);
 }
 
-// (sh, sl) += (ah, al): exact two-sum of the leading parts, rounding errors and low parts into sl
+// (sh, sl) += (ah, al): exact two-sum of the leading parts, rounding errors and low parts into sl,
+// then the pair renormalised (fast two-sum, |sl| <= half an ulp of sh) so that sl's own rounding
+// stays at 2^-48 of the sum instead of growing with the number of terms.  The _rn intrinsics keep
+// the compiler from contracting the two-sums into FMAs, which would break their exactness.
 __device__ __forceinline__ void ff_acc(float& sh, float& sl, float ah, float al)
 {
-    const float t = sh + ah;
-    const float bp = t - sh;
-    const float err = (sh - (t - bp)) + (ah - bp);
-    sl += err + al;
-    sh = t;
+    const float t = __fadd_rn(sh, ah);
+    const float bp = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(ah, bp));
+    const float lo = __fadd_rn(sl, __fadd_rn(err, al));
+    sh = __fadd_rn(t, lo);
+    sl = __fsub_rn(lo, __fsub_rn(sh, t));
 }
 
 // (sh, sl) += (xh + xl)(rh + rl): the leading product exact by an FMA, the cross terms in float
 // (the xl rl term, ~2^-48 of the product, is dropped)
 __device__ __forceinline__ void ff_fma_acc(float& sh, float& sl, float xh, float xl, float rh, float rl)
 {
-    const float p = xh * rh;
+    const float p = __fmul_rn(xh, rh);
     const float e = fmaf(xh, rh, -p);
     ff_acc(sh, sl, p, fmaf(xh, rl, fmaf(xl, rh, e)));
 }

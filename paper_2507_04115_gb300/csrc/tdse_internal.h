@@ -5,6 +5,8 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <limits>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "tdse.h"
@@ -48,6 +50,8 @@ struct GroupDesc {
     int32_t cls;          // class index
     int32_t N, P, K, m;   // grid size, warps carrying segments, halo, segment length
     int32_t I;            // instances per group (32, 16, 8, 4, 2 or 1)
+    int32_t w;            // cost of one time step (units of group_step_cost / 64, >= 1): the
+                          // scheduler's priority is remaining slices x w
 };
 
 // Device-side tables offsets inside a class block (in doubles).
@@ -89,6 +93,90 @@ inline int class_segments(int N, int K, int warps)
     return std::max(1, std::min(warps, max_P));
 }
 
+// Segment length of a group: P_g warps x L lanes per instance share the N points.
+inline int group_segment_length(int N, int P, int L) { return (N + P * L - 1) / (P * L); }
+
+// Warps carrying segments in a group of a class (N points, halo K) at L lanes per instance: the
+// class's segment rule for 32-wide groups; every warp of the CTA for lane-split groups (short
+// segments are the price of spreading an instance over more lanes).
+inline int group_warps(int N, int K, int L, int warps)
+{
+    return L == 1 ? class_segments(N, K, warps) : std::max(1, std::min(warps, N / L));
+}
+
+// Cost model of one time step of a group: ceil(P/4) x (27 m + 36 K) FP64 warp instructions on its
+// busiest SM sub-partition (27 per own point: forward elimination 16, back substitution and update
+// 11; 36 per halo point: 2K forward rows and K back-substitution rows), m = N / (P L).  One group
+// runs on one SM at a time.
+inline double group_step_cost(int N, int K, int L, int warps)
+{
+    const int P = group_warps(N, K, L, warps);
+    const int m = group_segment_length(N, P, L);
+    return std::ceil(P / 4.0) * (27.0 * m + 36.0 * (P * L > 1 ? K : 0));
+}
+
+// Group widths by the whole job's makespan.  A group of instances with Nt_max steps keeps one SM
+// busy for Nt_max x cost; groups migrate between SMs only between slices, so the job takes at least
+// max(sum of the groups' work / SMs, longest group).  When a few groups are much longer than the
+// rest (an uneven batch: long pulses on large grids), the longest group bounds the job; spreading
+// those instances over more lanes (L x 2 halves the instances per group, the group's step gets
+// cheaper at the price of more halo rows) shortens it.
+//   Per class c: N[c], K[c] (0: no halo, L stays 1), base L[c] (the per-step model's choice) and
+//   the instances' Nt sorted in decreasing order.  Groups are cut greedily from the longest
+//   instance: the group takes the smallest L >= base with Nt_first x cost <= T (32 at most) and
+//   the next 32/L instances.  T runs over S0 x 0.95^j (S0: the longest group of the base plan);
+//   the plan with the smallest makespan estimate is kept if it beats the base plan's by 5 %.
+//   widths[c] receives the L of every group of class c, in order.  Returns the estimate.
+struct WidthClass {
+    int N, K, L_base;
+    std::vector<int64_t> nt_desc;
+};
+
+inline double plan_widths_at(const std::vector<WidthClass>& cls, int warps, int sm_count, double T,
+                             std::vector<std::vector<int>>* widths)
+{
+    double work = 0.0, longest = 0.0;
+    if (widths) widths->assign(cls.size(), {});
+    for (size_t c = 0; c < cls.size(); ++c) {
+        const WidthClass& C = cls[c];
+        const int64_t n = (int64_t)C.nt_desc.size();
+        for (int64_t k = 0; k < n;) {
+            int L = C.L_base;
+            const double nt = (double)std::max<int64_t>(C.nt_desc[k], 1);
+            if (C.K > 0)
+                while (L < 32 && nt * group_step_cost(C.N, C.K, L, warps) > T) L *= 2;
+            const double t = nt * group_step_cost(C.N, C.K, L, warps);
+            work += t;
+            longest = std::max(longest, t);
+            if (widths) (*widths)[c].push_back(L);
+            k += 32 / L;
+        }
+    }
+    return std::max(work / std::max(1, sm_count), longest);
+}
+
+inline double plan_widths(const std::vector<WidthClass>& cls, int warps, int sm_count,
+                          std::vector<std::vector<int>>* widths)
+{
+    const double inf = std::numeric_limits<double>::infinity();
+    double S0 = 0.0;
+    for (const WidthClass& C : cls)
+        if (!C.nt_desc.empty())
+            S0 = std::max(S0, (double)std::max<int64_t>(C.nt_desc[0], 1) * group_step_cost(C.N, C.K, C.L_base, warps));
+    const double M0 = plan_widths_at(cls, warps, sm_count, inf, nullptr);
+    double best = M0, best_T = inf;
+    for (int j = 1; j <= 90; ++j) {
+        const double T = S0 * std::pow(0.95, j);
+        const double M = plan_widths_at(cls, warps, sm_count, T, nullptr);
+        if (M < best) {
+            best = M;
+            best_T = T;
+        }
+    }
+    if (!(best < 0.95 * M0)) best_T = inf;
+    return plan_widths_at(cls, warps, sm_count, best_T, widths);
+}
+
 // Function attributes (the dynamic shared memory limit) belong to a device: a launcher that raises
 // one keeps a flag per device ordinal and sets it on the first launch on each device.
 constexpr int kMaxAttrDevices = 64;
@@ -102,9 +190,6 @@ inline void attr_done(std::atomic<bool>* flags, int dev)
 {
     if (dev >= 0 && dev < kMaxAttrDevices) flags[dev].store(true, std::memory_order_release);
 }
-
-// Segment length of a group: P_g warps x L lanes per instance share the N points.
-inline int group_segment_length(int N, int P, int L) { return (N + P * L - 1) / (P * L); }
 
 // Stores the calling thread's last-error message (tdse_api.cu).
 const char* set_error_message(const char* msg);

@@ -118,9 +118,10 @@ __device__ __forceinline__ int64_t group_slices(const GroupDesc& G, int64_t step
     return step_begin == 0 ? 1 : 0;   // only the initial observables
 }
 
-// Warp 0 picks and claims the free group with the most remaining slices; ties go to the group
-// closest after this CTA's index (cyclically), so that CTAs starting together claim different
-// groups instead of all racing for the same one.  Returns the group (its slice index in *k_out) or
+// Warp 0 picks and claims the free group with the most remaining work (slices x the group's step
+// cost w: the longest groups of an uneven batch start first, so they do not finish last); ties go
+// to the group closest after this CTA's index (cyclically), so that CTAs starting together claim
+// different groups instead of all racing for the same one.  Returns the group (its slice index in *k_out) or
 // -1 when no free unfinished group is left.  Every failed claim means another CTA claimed a group,
 // so the retries are bounded by the total number of claims.
 __device__ __forceinline__ int pick_group(const GroupDesc* groups, int64_t n_groups, int* busy, int* progress, int64_t step_begin,
@@ -131,8 +132,8 @@ __device__ __forceinline__ int pick_group(const GroupDesc* groups, int64_t n_gro
     for (int64_t attempt = 0; attempt < 4 * n_groups + 64; ++attempt) {
         int64_t best_rem = 0, best_d = n_groups, best_g = -1;
         for (int64_t g = lane; g < n_groups; g += 32) {
-            const int64_t rem = group_slices(groups[g], step_begin, step_end, slice) -
-                                *(volatile int*)(progress + g);
+            const int64_t rem = (group_slices(groups[g], step_begin, step_end, slice) -
+                                 *(volatile int*)(progress + g)) * groups[g].w;
             const int64_t dist = (g - me + n_groups) % n_groups;
             if (rem > 0 && *(volatile int*)(busy + g) == 0 && (rem > best_rem || (rem == best_rem && dist < best_d))) {
                 best_rem = rem;

@@ -66,6 +66,7 @@ __global__ void k_static_setup(ClassDesc C, int64_t n_inst, int64_t n_groups, in
         G.K = K;
         G.m = m;
         G.I = kLanes;
+        G.w = 1;
         groups[g] = G;
     }
     for (int64_t s = tid; s < n_groups * kLanes; s += stride) {

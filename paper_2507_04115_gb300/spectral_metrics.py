@@ -26,6 +26,35 @@ def harmonic_cutoff(E0, omega, ip=0.579):
     return (ip + 3.17 * up) / omega
 
 
+def harmonic_powers(S, S_ref, omega0, dt, L, q_cut):
+    """[(h, power of S, power of S_ref)] over the odd harmonics h <= q_cut, the power summed over the
+    bins with h - 1/2 < q <= h + 1/2."""
+    S = np.asarray(S, dtype=np.float64)
+    S_ref = np.asarray(S_ref, dtype=np.float64)
+    q = np.arange(S.size) * 2 * np.pi / (L * dt) / omega0
+    out = []
+    for h in range(1, int(q_cut) + 1, 2):
+        win = (q > h - 0.5) & (q <= h + 0.5)
+        if win.any():
+            out.append((h, float(S[win].sum()), float(S_ref[win].sum())))
+    return out
+
+
+def plateau_errors_by_decades(S, S_ref, omega0, dt, L, q_cut, decades=(2, 4, 6, 8)):
+    """{D: worst relative error over the plateau harmonics 3 <= h <= q_cut whose reference power lies
+    within D decades of the strongest of them} (a diagnostic of how the error grows toward the
+    weakest harmonics)."""
+    rows = [(h, a, b) for h, a, b in harmonic_powers(S, S_ref, omega0, dt, L, q_cut) if h >= 3 and b > 0]
+    out = {}
+    if not rows:
+        return out
+    top = max(b for _, _, b in rows)
+    for D in decades:
+        errs = [abs(a - b) / b for _, a, b in rows if b >= top * 10.0 ** (-D)]
+        out[str(D)] = max(errs) if errs else 0.0
+    return out
+
+
 def spectral_errors(S, S_ref, omega0, dt, L, q_cut):
     """(relative L2 over q <= 1.5 q_cut, worst relative error over the odd harmonics within
     HARMONIC_DECADES decades of the strongest) of S against S_ref; bins k of an L-sample DFT."""

@@ -22,7 +22,7 @@ def env():
     return tdse, oracle
 
 
-def _rel(x, ref, floor=1e-5):   # floor: see test_gpu_parity._rel
+def _rel(x, ref, floor=1e-4):   # floor: see test_gpu_parity._rel
     return float(np.max(np.abs(np.asarray(x) - np.asarray(ref))) / max(np.max(np.abs(ref)), floor))
 
 
