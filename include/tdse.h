@@ -305,6 +305,8 @@ typedef struct {
     int64_t scratch_bytes;
     int64_t psi_bytes;
     int32_t lanes_per_instance;
+    double longest_share;   /* the planner's model: the longest group's time / (the whole batch's work
+                               / SMs); above 0.5 the longest group bounds the job at 2 CTAs per SM */
 } tdse_plan_info;
 
 tdse_status tdse_plan(const tdse_batch* batch, tdse_plan_info* info_host);

@@ -92,6 +92,7 @@ struct tdse_batch {
     std::vector<int64_t> slot_group;   // group of every slot
     int64_t n_slots = 0;
     int lanes_request = 0;             // tdse_set_layout's lanes per instance (0 = cost model)
+    double longest_share = 0.0;        // longest group's modelled time / (total work / SMs)
     // launch configuration of the persistent propagation kernel
     int warps_override = 0, ctas_per_sm_override = 0, slice_override = 0, max_ctas_override = 0;
     int warps = 8, ctas = 0, rows = 0, slice = 16, ring = 4;
@@ -348,10 +349,12 @@ tdse_status build_groups(tdse_batch* b)
     }
     for (int64_t k = 0; k < n_inst; ++k) wc[b->inst_class[order[k]]].nt_desc.push_back(b->n_steps[order[k]]);
     std::vector<std::vector<int>> widths;
+    double work = 0.0, longest = 0.0;
     if (b->lanes_request > 0)
-        plan_widths_at(wc, warps, b->sm_count, std::numeric_limits<double>::infinity(), &widths);
+        plan_widths_at(wc, warps, b->sm_count, std::numeric_limits<double>::infinity(), &widths, &work, &longest);
     else
-        plan_widths(wc, warps, b->sm_count, &widths);
+        plan_widths(wc, warps, b->sm_count, &widths, &work, &longest);
+    b->longest_share = work > 0.0 ? longest / (work / std::max(1, b->sm_count)) : 0.0;
     b->class_L.assign(n_cls, 1);
     for (int c = 0; c < n_cls; ++c)
         for (int Lg : widths[c]) b->class_L[c] = std::max(b->class_L[c], Lg);
@@ -680,6 +683,7 @@ tdse_status tdse_plan(const tdse_batch* b, tdse_plan_info* info)
     info->scratch_bytes = b->scratch_elems * (int64_t)b->cx_bytes();
     info->psi_bytes = b->psi_elems * (int64_t)b->cx_bytes();
     info->lanes_per_instance = b->class_L.empty() ? 1 : *std::max_element(b->class_L.begin(), b->class_L.end());
+    info->longest_share = b->longest_share;
     return TDSE_OK;
 }
 

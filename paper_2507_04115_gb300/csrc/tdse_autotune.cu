@@ -89,7 +89,10 @@ extern "C" tdse_status tdse_autotune(tdse_batch* b, const double* E_dev, double*
     };
 
     const int warps_grid[] = {4, 6, 8, 12, 16};
-    const int per_sm_grid[] = {1, 2};
+    // k CTAs per SM make each group's step ~k times longer (the SM is shared): when the longest
+    // group's time exceeds half the work per SM (an uneven batch), two CTAs per SM lengthen the job
+    // although the first steps, which the trials time, run faster
+    const int per_sm_grid[] = {1, p0.longest_share > 0.5 ? 1 : 2};
     bool first = true;
     for (int w : warps_grid)
         for (int c : per_sm_grid) {

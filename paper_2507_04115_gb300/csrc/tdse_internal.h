@@ -133,7 +133,8 @@ struct WidthClass {
 };
 
 inline double plan_widths_at(const std::vector<WidthClass>& cls, int warps, int sm_count, double T,
-                             std::vector<std::vector<int>>* widths)
+                             std::vector<std::vector<int>>* widths, double* work_out = nullptr,
+                             double* longest_out = nullptr)
 {
     double work = 0.0, longest = 0.0;
     if (widths) widths->assign(cls.size(), {});
@@ -152,11 +153,14 @@ inline double plan_widths_at(const std::vector<WidthClass>& cls, int warps, int 
             k += 32 / L;
         }
     }
+    if (work_out) *work_out = work;
+    if (longest_out) *longest_out = longest;
     return std::max(work / std::max(1, sm_count), longest);
 }
 
 inline double plan_widths(const std::vector<WidthClass>& cls, int warps, int sm_count,
-                          std::vector<std::vector<int>>* widths)
+                          std::vector<std::vector<int>>* widths, double* work_out = nullptr,
+                          double* longest_out = nullptr)
 {
     const double inf = std::numeric_limits<double>::infinity();
     double S0 = 0.0;
@@ -174,7 +178,7 @@ inline double plan_widths(const std::vector<WidthClass>& cls, int warps, int sm_
         }
     }
     if (!(best < 0.95 * M0)) best_T = inf;
-    return plan_widths_at(cls, warps, sm_count, best_T, widths);
+    return plan_widths_at(cls, warps, sm_count, best_T, widths, work_out, longest_out);
 }
 
 // Function attributes (the dynamic shared memory limit) belong to a device: a launcher that raises

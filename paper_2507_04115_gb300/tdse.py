@@ -40,7 +40,7 @@ class tdse_plan_info(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int64), ("segments", ctypes.c_int32), ("halo", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas", ctypes.c_int32), ("slice_steps", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64), ("psi_bytes", ctypes.c_int64),
-                ("lanes_per_instance", ctypes.c_int32)]
+                ("lanes_per_instance", ctypes.c_int32), ("longest_share", ctypes.c_double)]
 
 
 class tdse_pipe_rates(ctypes.Structure):
@@ -267,7 +267,7 @@ class Batch:
         return dict(n_groups=info.n_groups, segments=info.segments, halo=info.halo,
                     warps_per_cta=info.warps_per_cta, ctas=info.ctas, slice_steps=info.slice_steps,
                     scratch_bytes=info.scratch_bytes, psi_bytes=info.psi_bytes,
-                    lanes_per_instance=info.lanes_per_instance)
+                    lanes_per_instance=info.lanes_per_instance, longest_share=info.longest_share)
 
     def energy_distribution(self, E_grid, epsilon, out=None, stream=None):
         """P[i, k]: energy distribution of instance i's current state at E_grid[k] with resolution

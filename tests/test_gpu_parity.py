@@ -682,7 +682,10 @@ def test_group_widths_mixed_in_one_launch(env):
     soft = np.where(dx == 0.15, 1.19, 1.2)
     nt = np.concatenate([np.full(nA, 60), rng.integers(2600, 3000, nB)])
     w = inputs.omega_from_wavelength_nm(800.0)
-    rows = [inputs.sin2_pulse(int(nt[i]), dt, rng.uniform(0.03, 0.09), w, 0.5 if i < nA else 2.0, 0.0)
+    # the short class gets a whole (sub-cycle) envelope within its 60 steps, so that its dipole is a
+    # developed signal rather than rounding noise (the MIXED comparison is relative to the signal)
+    rows = [inputs.sin2_pulse(int(nt[i]), dt, rng.uniform(0.03, 0.09), w,
+                              nt[i] * dt * w / (2 * np.pi) if i < nA else 2.0, 0.0)
             for i in range(nA + nB)]
     offs = np.concatenate([[0], np.cumsum(nt + 1)])
     dev = torch.device("cuda", 0)
