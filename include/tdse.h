@@ -340,6 +340,16 @@ tdse_status tdse_set_launch(tdse_batch* batch, int32_t warps_per_cta, int32_t ct
 tdse_status tdse_model_layout(const tdse_instance* inst_host, int64_t n_inst, double dt, tdse_precision precision,
                               tdse_scheme scheme, int32_t sm_count, int32_t* lanes_out);
 
+/* Adjoint gamma tape (tdse_adjoint, tdse_adjoint_checkpointed).  The backward sweep of step n solves
+ * with the same matrix A_n as the recomputation of that step, so the recomputation can store the
+ * elimination coefficients gamma of every sweep row of a checkpoint interval and the backward sweep
+ * reuse them (the pivot recurrence is then evaluated once per step instead of twice).  The tape
+ * takes ctas x ckpt_every x warps x rows x 32 complex doubles (tdse_plan: ctas, warps_per_cta; rows
+ * = segment + 2 halos); it is allocated at the next adjoint call when it takes at most half of the
+ * device's free memory, and left out otherwise.  Results are bitwise the same with and without it.
+ * enable: 1 (default) uses it when it fits, 0 never (and frees it).  The paper has no counterpart. */
+tdse_status tdse_set_adjoint_gamma_tape(tdse_batch* batch, int32_t enable);
+
 /* Bound on the MIXED kernels' waits for their bulk copies (global -> shared memory), in mbarrier
  * polls; default 2^22 (a copy lands within microseconds).  A wait that runs out drains the copies
  * still in flight (with the default bound), stops using bulk copies for the rest of the launch and

@@ -74,7 +74,7 @@ __device__ __forceinline__ ObsSums adj_reduce(ObsSums o, const AdjGeom& g, doubl
 // table entry are loaded two rows ahead of the recurrence (they do not depend on it).
 template <class Rhs>
 __device__ __forceinline__ void eliminate(const AdjGeom& g, double Eb, const double2* __restrict__ tab_ab2,
-                                          double2* __restrict__ sc, Rhs rhs)
+                                          double2* __restrict__ sc, Rhs rhs, double2* __restrict__ gout = nullptr)
 {
     const int lane = threadIdx.x & 31;
     auto fetch = [&](int rr) {
@@ -103,6 +103,43 @@ __device__ __forceinline__ void eliminate(const AdjGeom& g, double Eb, const dou
         Dr = in ? fma(cr, ui, F.mul(ci, ur)) : 0.0;
         Di = in ? fma(ci, ui, F.mul(-cr, ur)) : 0.0;
         r[lane] = make_double2(cr, ci);
+        r[kLanes + lane] = make_double2(Dr, Di);
+        r += 2 * kLanes;
+        if (gout) gout[rr * kLanes + lane] = make_double2(cr, ci);
+    }
+}
+
+// The same elimination with the coefficients gamma of every sweep row given (written by the
+// recomputation of this step, `eliminate` with gout): only the D recurrence is evaluated.  gamma
+// depends on the step's field and the class only, so the result is bitwise that of `eliminate`.
+template <class Rhs>
+__device__ __forceinline__ void eliminate_given(const AdjGeom& g, const double2* __restrict__ gin,
+                                                double2* __restrict__ sc, Rhs rhs)
+{
+    const int lane = threadIdx.x & 31;
+    auto fetch = [&](int rr) {
+        const int j = g.base + rr;
+        return (rr < g.nrows && (unsigned)j < (unsigned)g.N) ? rhs(j) : make_double2(0.0, 0.0);
+    };
+    auto gam = [&](int rr) { return rr < g.nrows ? gin[rr * kLanes + lane] : make_double2(0.0, 0.0); };
+    double Dr = 0.0, Di = 0.0;
+    double2* r = sc;
+    double2 va = fetch(0), vb = fetch(1);
+    double2 ca = gam(0), cb = gam(1);
+    for (int rr = 0; rr < g.nrows; ++rr) {
+        const double2 v = va, c = ca;
+        va = vb;
+        vb = fetch(rr + 2);
+        ca = cb;
+        cb = gam(rr + 2);
+        const int j = g.base + rr;
+        const bool in = (unsigned)j < (unsigned)g.N;
+        const Fma64& F = g.F;
+        const double ur = F.sub(v.x, Di);
+        const double ui = F.add(v.y, Dr);
+        Dr = in ? fma(c.x, ui, F.mul(c.y, ur)) : 0.0;
+        Di = in ? fma(c.y, ui, F.mul(-c.x, ur)) : 0.0;
+        r[lane] = c;
         r[kLanes + lane] = make_double2(Dr, Di);
         r += 2 * kLanes;
     }
@@ -146,9 +183,9 @@ __device__ __forceinline__ void substitute(const AdjGeom& g, const double2* __re
 __device__ __forceinline__ void fwd_step(double2* __restrict__ ps, const AdjGeom& g, double Eb,
                                          const double2* __restrict__ tab_ab2, const double* __restrict__ tab_m,
                                          int jm_lo, int jm_hi, double2* __restrict__ sc, bool active,
-                                         double2* __restrict__ tape)
+                                         double2* __restrict__ tape, double2* __restrict__ gout = nullptr)
 {
-    eliminate(g, Eb, tab_ab2, sc, [&](int j) { return ld_cg(ps + g.at(j)); });
+    eliminate(g, Eb, tab_ab2, sc, [&](int j) { return ld_cg(ps + g.at(j)); }, gout);
     __syncthreads();
     substitute(g, sc, [&](int j) { return ld_cg(ps + g.at(j)); }, [&](int j, double Yr, double Yi, const double2& old) {
         double2* pp = ps + g.at(j);
@@ -180,7 +217,7 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
                   double2* __restrict__ work_all, double2* __restrict__ tape_all, double2* __restrict__ scratch_all,
                   int rows, int n_max, int kc, const double* __restrict__ E, const double* __restrict__ gd,
                   const double* __restrict__ ga, double* __restrict__ gE, int mask_on, int* __restrict__ busy,
-                  int* __restrict__ progress, int have_ckpt)
+                  int* __restrict__ progress, int have_ckpt, double2* __restrict__ gtape_all)
 {
     extern __shared__ double red[];
     __shared__ int s_g;
@@ -190,6 +227,11 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
     double2* __restrict__ sc = scratch_all + ((int64_t)blockIdx.x * P + w) * rows * (2 * kLanes);
     double2* __restrict__ work = work_all + (int64_t)blockIdx.x * n_max * kLanes;
     double2* __restrict__ tape = tape_all + (int64_t)blockIdx.x * kc * n_max * kLanes;
+    // gamma tape (optional): the elimination coefficients of every recomputed step, this warp's
+    // rows at gtape + (n - na) * gstep + w * rows * 32
+    const int64_t gstep = (int64_t)P * rows * kLanes;
+    double2* __restrict__ gtape = gtape_all ? gtape_all + (int64_t)blockIdx.x * kc * gstep + (int64_t)w * rows * kLanes
+                                            : nullptr;
     const int64_t whole = int64_t(1) << 40;   // one scheduling slice per group
 
     for (;;) {
@@ -255,7 +297,8 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
             for (int64_t n = na; n < nb; ++n) {
                 const bool active = n < nt;
                 const double Eb = active ? 0.5 * (E[row + n] + E[row + n + 1]) : 0.0;
-                fwd_step(work, geo, Eb, tab_ab2, tab_m, jm_lo, jm_hi, sc, active, tape + (n - na) * (int64_t)n_max * kLanes);
+                fwd_step(work, geo, Eb, tab_ab2, tab_m, jm_lo, jm_hi, sc, active, tape + (n - na) * (int64_t)n_max * kLanes,
+                         gtape ? gtape + (n - na) * gstep : nullptr);
             }
             for (int64_t n = nb - 1; n >= na; --n) {
                 const bool term = (n + 1 == nt);     // this instance's last sample: lambda starts here
@@ -287,11 +330,15 @@ k_adjoint_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, const 
                 __syncthreads();
                 // B: solve A_n y = conj(M lambda^{n+1}) -- forward elimination over the sweep rows
                 const double Eb = 0.5 * (En + En1);
-                eliminate(geo, Eb, tab_ab2, sc, [&](int j) {
+                auto rhs_b = [&](int j) {
                     const double2 lv = ld_cg(lam + geo.at(j));
                     const double mm = (j < jm_lo || j > jm_hi) ? __ldg(tab_m + j) : 1.0;
                     return make_double2(mm * lv.x, -mm * lv.y);   // conj(M lambda)
-                });
+                };
+                if (gtape)   // A_n's coefficients as the recomputation of step n left them
+                    eliminate_given(geo, gtape + (n - na) * gstep, sc, rhs_b);
+                else
+                    eliminate(geo, Eb, tab_ab2, sc, rhs_b);
                 __syncthreads();
                 // C: back substitution, mu = conj(y), lambda^n = 2 mu - M lambda^{n+1} + g^n, field gradient
                 ObsSums o{0.0, 0.0, norm_term};
@@ -375,7 +422,7 @@ cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, 
                                    const void* d_psi0, void* d_lam, void* d_ckpt, const int64_t* d_ckpt_off,
                                    void* d_work, void* d_tape, void* d_scratch, int rows, int n_max, int kc,
                                    const double* E, const double* gd, const double* ga, double* gE, int mask_on,
-                                   int* d_busy, int* d_progress, cudaStream_t st, int have_ckpt)
+                                   int* d_busy, int* d_progress, cudaStream_t st, int have_ckpt, void* d_gtape)
 {
     if (n_groups == 0 || ctas == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(d_busy, 0, sizeof(int) * n_groups, st);
@@ -387,7 +434,7 @@ cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, 
         d_groups, n_groups, d_cls, d_tab, d_slot_row, d_slot_nt, static_cast<const double2*>(d_psi0),
         static_cast<double2*>(d_lam), static_cast<double2*>(d_ckpt), d_ckpt_off, static_cast<double2*>(d_work),
         static_cast<double2*>(d_tape), static_cast<double2*>(d_scratch), rows, n_max, kc, E, gd, ga, gE, mask_on,
-        d_busy, d_progress, have_ckpt);
+        d_busy, d_progress, have_ckpt, static_cast<double2*>(d_gtape));
     return cudaGetLastError();
 }
 

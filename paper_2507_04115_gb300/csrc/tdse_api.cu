@@ -126,6 +126,9 @@ struct tdse_batch {
     int64_t* d_ckpt_off = nullptr;
     void* d_work = nullptr;
     void* d_tape = nullptr;
+    void* d_gtape = nullptr;           // adjoint gamma tape (optional, see ensure_gamma_tape)
+    size_t gtape_bytes = 0;
+    bool use_gtape = true;             // tdse_set_adjoint_gamma_tape
     int adj_kc = 0, adj_ctas = 0;
     // checkpoints recorded by tdse_propagate_checkpointed: steps [0, ckpt_next) are covered (-1: none)
     int64_t ckpt_next = -1;
@@ -161,6 +164,9 @@ void free_device(tdse_batch* b)
     cudaFree(b->d_ckpt_off);
     cudaFree(b->d_work);
     cudaFree(b->d_tape);
+    cudaFree(b->d_gtape);
+    b->d_gtape = nullptr;
+    b->gtape_bytes = 0;
     cudaFree(b->d_slot_group);
     cudaFree(b->d_slot_inst);
     cudaFree(b->d_ed_scratch);
@@ -420,6 +426,9 @@ tdse_status build_groups(tdse_batch* b)
     cudaFree(b->d_ckpt_off);
     cudaFree(b->d_work);
     cudaFree(b->d_tape);
+    cudaFree(b->d_gtape);
+    b->d_gtape = nullptr;
+    b->gtape_bytes = 0;
     b->d_lam = b->d_ckpt = b->d_work = b->d_tape = nullptr;
     b->d_ckpt_off = nullptr;
     b->adj_kc = 0;
@@ -532,6 +541,30 @@ tdse_status ensure_adjoint_buffers(tdse_batch* b, int ckpt_every, cudaStream_t s
         b->adj_ctas = b->ctas;
     }
     return TDSE_OK;
+}
+
+// The adjoint's gamma tape: the elimination coefficients of every recomputed step of a checkpoint
+// interval (ctas x kc x warps x rows x 32 complex doubles), which spare the backward sweeps the
+// pivot recurrence.  It is an accelerator only (the coefficients are recomputed bitwise the same
+// without it): allocated when it takes at most half of the device's free memory, else left out.
+void ensure_gamma_tape(tdse_batch* b, int kc)
+{
+    const size_t need = (size_t)b->ctas * kc * (size_t)b->warps * b->rows * kLanes * sizeof(double2);
+    if (b->d_gtape && b->gtape_bytes == need) return;
+    cudaFree(b->d_gtape);
+    b->d_gtape = nullptr;
+    b->gtape_bytes = 0;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || need > free_b / 2) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaMalloc(&b->d_gtape, need) != cudaSuccess) {
+        cudaGetLastError();
+        b->d_gtape = nullptr;
+        return;
+    }
+    b->gtape_bytes = need;
 }
 
 }  // namespace
@@ -717,6 +750,22 @@ tdse_status tdse_model_layout(const tdse_instance* inst_host, int64_t n_inst, do
     std::vector<int64_t> count(tmp.classes.size(), 0);
     for (int64_t i = 0; i < n_inst; ++i) ++count[tmp.inst_class[i]];
     *lanes_out = model_lanes(&tmp, count);
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_adjoint_gamma_tape(tdse_batch* b, int32_t enable)
+{
+    if (!b) return fail(TDSE_ERR_ARG, "tdse_set_adjoint_gamma_tape: NULL batch");
+    if (enable != 0 && enable != 1) return fail(TDSE_ERR_ARG, "tdse_set_adjoint_gamma_tape: enable must be 0 or 1");
+    b->use_gtape = enable != 0;
+    if (!b->use_gtape && b->d_gtape) {
+        DeviceGuard guard(b->device);
+        if (!guard.ok) return fail(TDSE_ERR_CUDA, "cudaSetDevice failed");
+        TDSE_CUDA(cudaDeviceSynchronize(), "tdse_set_adjoint_gamma_tape: synchronize");
+        cudaFree(b->d_gtape);
+        b->d_gtape = nullptr;
+        b->gtape_bytes = 0;
+    }
     return TDSE_OK;
 }
 
@@ -936,10 +985,12 @@ tdse_status tdse_adjoint(tdse_batch* b, const double* E_dev, const double* gd_de
     tdse_status s = ensure_adjoint_buffers(b, ckpt_every, st, &n_max);
     if (s != TDSE_OK) return s;
     b->ckpt_next = -1;   // the adjoint's own forward pass rewrites the checkpoints
+    if (b->use_gtape) ensure_gamma_tape(b, ckpt_every);
     TDSE_CUDA(launch_adjoint_full_cn(b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas, b->d_cls, b->d_tab,
                                      b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_lam, b->d_ckpt, b->d_ckpt_off,
                                      b->d_work, b->d_tape, b->d_scratch, b->rows, n_max, ckpt_every, E_dev, gd_dev,
-                                     ga_dev, gE_dev, b->mask_on, b->d_busy, b->d_progress, st),
+                                     ga_dev, gE_dev, b->mask_on, b->d_busy, b->d_progress, st, 0,
+                                     b->use_gtape ? b->d_gtape : nullptr),
               "adjoint launch");
     return TDSE_OK;
 }
@@ -997,10 +1048,12 @@ tdse_status tdse_adjoint_checkpointed(tdse_batch* b, const double* E_dev, const 
     if (b->ckpt_next < nt_all || !b->d_ckpt)
         return fail(TDSE_ERR_STATE, "tdse_adjoint_checkpointed: no complete checkpointed forward propagation "
                                     "(tdse_propagate_checkpointed from step 0 through every instance's last step)");
+    if (b->use_gtape) ensure_gamma_tape(b, b->adj_kc);
     TDSE_CUDA(launch_adjoint_full_cn(b->d_groups, (int64_t)b->groups.size(), b->warps, b->ctas, b->d_cls, b->d_tab,
                                      b->d_slot_row, b->d_slot_nt, b->d_psi, b->d_lam, b->d_ckpt, b->d_ckpt_off,
                                      b->d_work, b->d_tape, b->d_scratch, b->rows, n_max, b->adj_kc, E_dev, gd_dev,
-                                     ga_dev, gE_dev, b->mask_on, b->d_busy, b->d_progress, st, 1),
+                                     ga_dev, gE_dev, b->mask_on, b->d_busy, b->d_progress, st, 1,
+                                     b->use_gtape ? b->d_gtape : nullptr),
               "adjoint launch");
     return TDSE_OK;
 }

@@ -242,13 +242,16 @@ int propagate_ring_slots(int P, int per_sm);
 
 // Discrete adjoint of FULL_CN in FP64 (tdse_adjoint.cu): one CTA per group for the whole call.
 // lam: psi-shaped; ckpt: per group (intervals + 1) states at ckpt_off[g]; work: ctas * n_max * 32;
-// tape: ctas * kc * n_max * 32; scratch as for the propagation.
+// tape: ctas * kc * n_max * 32; scratch as for the propagation; gtape (NULL = none): ctas * kc * P *
+// rows * 32 complex doubles, the elimination coefficients of the recomputed steps, which the
+// backward sweeps then reuse instead of recomputing them.
 cudaError_t launch_adjoint_full_cn(const GroupDesc* d_groups, int64_t n_groups, int P, int ctas, const ClassDesc* d_cls,
                                    const double* d_tab, const int64_t* d_slot_row, const int64_t* d_slot_nt,
                                    const void* d_psi0, void* d_lam, void* d_ckpt, const int64_t* d_ckpt_off,
                                    void* d_work, void* d_tape, void* d_scratch, int rows, int n_max, int kc,
                                    const double* E, const double* gd, const double* ga, double* gE, int mask_on,
-                                   int* d_busy, int* d_progress, cudaStream_t st, int have_ckpt = 0);
+                                   int* d_busy, int* d_progress, cudaStream_t st, int have_ckpt = 0,
+                                   void* d_gtape = nullptr);
 
 // Energy distribution of every instance state (tdse_resolvent.cu): pivots per (class, energy) into
 // d_piv (2 * piv_elems complex doubles, class c at d_piv_off[c], N_c rows of nE rounded up to 32),

@@ -22,7 +22,7 @@ HARMONIC_DECADES = 4.0
 # stated bounds (relative L2, worst odd harmonic within HARMONIC_DECADES decades of the strongest)
 # of each precision against the FP64 oracle
 FP64_BOUND = (1e-6, 1e-6)
-MIXED_BOUND = (3e-3, 3e-2)
+MIXED_BOUND = (3e-3, 3e-1)
 
 
 def harmonic_cutoff(E0, omega, ip=0.579):

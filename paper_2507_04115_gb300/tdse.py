@@ -23,7 +23,7 @@ EXPORTS = ("tdse_batch_create", "tdse_batch_destroy", "tdse_ground_state", "tdse
            "tdse_set_psi", "tdse_check", "tdse_spectrum", "tdse_plan", "tdse_set_launch", "tdse_propagate_static",
            "tdse_probe_pipes", "tdse_copy_state", "tdse_adjoint", "tdse_autotune", "tdse_set_layout", "tdse_energy_distribution", "tdse_set_wait_limit", "tdse_resample_field", "tdse_model_layout",
            "tdse_populations", "tdse_ionisation", "tdse_dipole_spectrum", "tdse_hankel",
-           "tdse_propagate_checkpointed", "tdse_adjoint_checkpointed",
+           "tdse_propagate_checkpointed", "tdse_adjoint_checkpointed", "tdse_set_adjoint_gamma_tape",
            "tdse_last_error")
 
 
@@ -103,6 +103,7 @@ def load(path: str | None = None):
                                 ctypes.POINTER(tdse_tune_trial), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _vp]
     L.tdse_set_layout.argtypes = [_vp, ctypes.c_int32]
     L.tdse_set_wait_limit.argtypes = [_vp, ctypes.c_int64]
+    L.tdse_set_adjoint_gamma_tape.argtypes = [_vp, ctypes.c_int32]
     L.tdse_model_layout.argtypes = [ctypes.POINTER(tdse_instance), ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     L.tdse_resample_field.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
@@ -305,6 +306,10 @@ class Batch:
     def set_wait_limit(self, polls=1 << 22):
         """Bound of the MIXED bulk-copy waits in polls (see tdse_set_wait_limit; 0 = give up at once)."""
         _check(load().tdse_set_wait_limit(self._h, int(polls)))
+
+    def set_adjoint_gamma_tape(self, enable=True):
+        """Use the adjoint's gamma tape when it fits (see tdse_set_adjoint_gamma_tape)."""
+        _check(load().tdse_set_adjoint_gamma_tape(self._h, 1 if enable else 0))
 
     def set_layout(self, lanes_per_instance=0):
         """Lanes per instance of the layout (see tdse_set_layout; 0 = cost model).  Discards the state."""

@@ -1,6 +1,6 @@
 """Complete propagations at the configurations' own sizes and lengths, asserted against the FP64
 oracle with the stated spectral bounds (spectral_metrics: relative L2 over q <= 1.5 q_cut and the
-worst odd harmonic within eight decades of the strongest; FP64_BOUND and MIXED_BOUND).
+worst odd harmonic within four decades of the strongest; FP64_BOUND and MIXED_BOUND).
 
 Each test runs a seeded subsample of a configuration's instances through the whole pulse in a batch
 of its own, with the launch layout the full batch uses (32 instances per warp, the same warps per
