@@ -74,6 +74,7 @@ def test_null_handles_are_rejected(lib):
     assert n.value == -1
     assert lib.tdse_energy_distribution(None, None, 4, 0.05, None, None) == tdse.TDSE_ERR_ARG
     assert lib.tdse_set_wait_limit(None, 10) == tdse.TDSE_ERR_ARG
+    assert lib.tdse_set_adjoint_gamma_tape(None, 1) == tdse.TDSE_ERR_ARG
     assert lib.tdse_populations(None, 1.0, None, None) == tdse.TDSE_ERR_ARG
     assert lib.tdse_resample_field(None, 1, 8, 0.1, 0.01, 10, 10, None, 0, None) == tdse.TDSE_ERR_ARG
     lib.tdse_batch_destroy(None)
