@@ -48,7 +48,7 @@ struct Fma64 {
 // ---- float pairs on the FP32 pipe (no FP64 instruction; GB300 runs FP32 at 64x its FP64 rate) ----
 
 // v >= 0 (a squared modulus) as h + l with h, l floats: h its leading 24 significant bits, l the rest
-// truncated to 24 bits, so |h + l - v| < 2^-47 v + 2^-126 (parts below float's normal range flush
+// rounded to 24 bits, so |h + l - v| <= 2^-48 v + 2^-126 (parts below float's normal range flush
 // to zero).  Integer operations on the double's two words only.  Infinity and NaN map to a float infinity or NaN; values beyond float's range to infinity,
 // so a non-finite state still shows in the sums.
 __device__ __forceinline__ void split_ff(double v, float& h, float& l)
@@ -67,8 +67,40 @@ __device__ __forceinline__ void split_ff(double v, float& h, float& l)
     const unsigned long long t = ((unsigned long long)m29 << (lz + 1)) & 0xffffffffull;
     const int fe = (int)e - 917 - lz;
     unsigned lb = ((unsigned)fe << 23) | (unsigned)(t >> 9);
+    lb += (unsigned)(t >> 8) & 1u;   // l rounded to nearest (a carry into the exponent is exact)
     lb = (m29 == 0u || fe <= 0 || e < 897u || special) ? 0u : lb;
     l = __uint_as_float(lb);
+}
+
+// Any finite v as h + l with h, l floats of v's sign: the split of |v| above (|h + l - v| <= 2^-48 |v|
+// + 2^-126), the sign bit copied onto both.  Integer operations only.
+__device__ __forceinline__ void split_sf(double v, float& h, float& l)
+{
+    const int hi = __double2hiint(v);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    split_ff(__hiloint2double(hi & 0x7fffffff, __double2loint(v)), h, l);   // |v| by clearing the sign bit
+    h = __uint_as_float(__float_as_uint(h) | sign);
+    l = __uint_as_float(__float_as_uint(l) | sign);
+}
+
+// |x|^2 = xr^2 + xi^2 as a float pair (rh, rl), within 2^-44 relative (plus 2^-124 absolute: squares
+// below float's normal range flush), on the FP32 pipe: xr and xi are
+// split into float pairs by integer operations, the squares of the leading parts are exact with
+// their FMA residuals, and the rest, (2h + l) l, is added in float.
+__device__ __forceinline__ void sq_mod_ff(double xr, double xi, float& rh, float& rl)
+{
+    float ah, al, bh, bl;
+    split_sf(xr, ah, al);
+    split_sf(xi, bh, bl);
+    const float p1 = __fmul_rn(ah, ah), p2 = __fmul_rn(bh, bh);
+    const float e1 = fmaf(ah, ah, -p1), e2 = fmaf(bh, bh, -p2);
+    const float s = __fadd_rn(p1, p2);
+    const float bp = __fsub_rn(s, p1);
+    const float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bp)), __fsub_rn(p2, bp));
+    const float c = fmaf(2.0f * ah + al, al, __fmul_rn(2.0f * bh + bl, bl));   // (2h + l) l
+    const float lo = __fadd_rn(__fadd_rn(t, __fadd_rn(e1, e2)), c);
+    rh = __fadd_rn(s, lo);
+    rl = __fsub_rn(lo, __fsub_rn(rh, s));
 }
 
 // float -> double by integer operations (exact for normal floats and infinities/NaN; zero and

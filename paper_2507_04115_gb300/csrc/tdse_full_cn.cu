@@ -546,10 +546,10 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 const Cx* pl = pw - 2 * kLanes;                        // psi_{j-2} (prefetch)
                 const double* tm = tab_m + (e - 1);
                 const float4* txf = reinterpret_cast<const float4*>(tab + tab_xff(C)) + (e - 1);
-                // observable sums: rho = |psi|^2 in double, split into a float pair, summed as float
-                // pairs over blocks of kObsBlock points on the FP32 pipe (with x and dV/dx as float
-                // pairs), each block's pair widened to double (integer operations) and added in
-                // double: 2 FP64 instructions per block and sum instead of 1 per point and sum
+                // observable sums: rho = |psi|^2 as a float pair (sq_mod_ff), summed as float pairs
+                // over blocks of kObsBlock points on the FP32 pipe (with x and dV/dx as float pairs),
+                // each block's pair widened to double (integer operations) and added in double: no
+                // FP64 instruction per point, 2 per block and sum
                 float snh = 0.f, snl = 0.f, sxh = 0.f, sxl = 0.f, svh = 0.f, svl = 0.f;
                 int blk = 0;
                 if (e - 1 >= s) {
@@ -588,9 +588,8 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                     --tm;
                     if (active) *pw = mk(xr, xi);
                     pw -= kLanes;
-                    const double rho = fma(xr, xr, F.mul(xi, xi));
-                    float rh, rl;
-                    split_ff(rho, rh, rl);
+                    float rh, rl;   // rho = |psi|^2 as a float pair, off the FP64 pipe
+                    sq_mod_ff(xr, xi, rh, rl);
                     const float4 xf = __ldg(txf);
                     --txf;
                     ff_acc(snh, snl, rh, rl);

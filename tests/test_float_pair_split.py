@@ -1,7 +1,8 @@
 """The integer float-pair split and widening the propagation kernels use for their observable sums
 (no GPU): a numpy restatement of the bit operations on the double's and the float's words, checked
-against the bounds their comments state, |h + l - v| < 2^-47 v + 2^-126 for the split of v >= 0 and
-exactness of the widening, with infinities and NaN carried through."""
+against the bounds their comments state: |h + l - v| <= 2^-48 v + 2^-126 for the split of v >= 0,
+|x|^2 as a float pair within 2^-44 relative, exactness of the widening, with infinities and NaN
+carried through."""
 import numpy as np
 
 
@@ -20,6 +21,7 @@ def _split(v):
     t = (m29 << (lz + 1)) & 0xffffffff
     fe = e - 917 - lz
     lb = (fe << 23) | (t >> 9)
+    lb = lb + ((t >> 8) & 1)
     lb = np.where((m29 == 0) | (fe <= 0) | (e < 897) | special, 0, lb)
     h = (hb & 0xffffffff).astype(np.uint32).view(np.float32)
     l = (lb & 0xffffffff).astype(np.uint32).view(np.float32)
@@ -50,8 +52,8 @@ def test_split_bound_over_the_whole_range():
     assert np.all(np.isfinite(h)) and np.all(np.isfinite(l)) and np.all(l >= 0)
     # h exact as the leading bits: the split is exact where the remaining bits fit
     err = np.abs(h.astype(np.float64) + l.astype(np.float64) - v)
-    assert np.all(err < 2.0 ** -47 * v + 2.0 ** -126)
-    # the bound is nearly reached (so a split that dropped l would fail)
+    assert np.all(err <= 2.0 ** -48 * v + 2.0 ** -126)
+    # the bound is nearly reached (so a split that dropped or truncated l would fail)
     assert np.max(err[v > 1e-30] / v[v > 1e-30]) > 2.0 ** -50
     h0, _ = _split(v[v > 1e-30])
     assert np.max(np.abs(h0.astype(np.float64) - v[v > 1e-30]) / v[v > 1e-30]) > 2.0 ** -26
@@ -73,3 +75,45 @@ def test_widening_is_exact():
     assert np.array_equal(w, f.astype(np.float64))
     s = _widen(np.array([np.inf, -np.inf, np.nan, np.float32(1e-40)], dtype=np.float32))
     assert s[0] == np.inf and s[1] == -np.inf and np.isnan(s[2]) and s[3] == 0.0
+
+
+def _split_signed(v):
+    v = np.asarray(v, dtype=np.float64)
+    h, l = _split(np.abs(v))
+    sgn = np.signbit(v)
+    return np.where(sgn, -h, h).astype(np.float32), np.where(sgn, -l, l).astype(np.float32)
+
+
+def _sq_mod(xr, xi):
+    """The kernels' |x|^2 as a float pair (sq_mod_ff), restated with float32 operations; the FMA
+    residuals are formed exactly in float64 (an FMA rounds once)."""
+    f = np.float32
+    ah, al = _split_signed(xr)
+    bh, bl = _split_signed(xi)
+    p1, p2 = (ah * ah).astype(f), (bh * bh).astype(f)
+    e1 = (ah.astype(np.float64) ** 2 - p1).astype(f)
+    e2 = (bh.astype(np.float64) ** 2 - p2).astype(f)
+    s = (p1 + p2).astype(f)
+    bp = (s - p1).astype(f)
+    t = ((p1 - (s - bp).astype(f)).astype(f) + (p2 - bp).astype(f)).astype(f)
+    c = (np.float64((f(2) * ah + al).astype(f)) * al + ((f(2) * bh + bl).astype(f) * bl).astype(f)).astype(f)
+    lo = ((t + (e1 + e2).astype(f)).astype(f) + c).astype(f)
+    rh = (s + lo).astype(f)
+    rl = (lo - (rh - s).astype(f)).astype(f)
+    return rh, rl
+
+
+def test_squared_modulus_pair_bound():
+    rng = np.random.default_rng(19)
+    scale = np.exp(rng.uniform(np.log(1e-18), np.log(10.0), 200000))
+    xr = rng.standard_normal(scale.size) * scale
+    xi = rng.standard_normal(scale.size) * scale
+    rh, rl = _sq_mod(xr, xi)
+    exact = xr.astype(np.longdouble) ** 2 + xi.astype(np.longdouble) ** 2
+    err = np.abs(rh.astype(np.longdouble) + rl.astype(np.longdouble) - exact)
+    # relative 2^-45, and an absolute floor below float's normal range (squares of parts under 2^-63)
+    assert np.all(err < 2.0 ** -44 * exact + 2.0 ** -124)
+    assert float(np.max(err[exact > 1e-30] / exact[exact > 1e-30])) < 2.0 ** -44
+    # the signed split keeps the sign on both parts
+    h, l = _split_signed(np.array([-1.0 / 3.0, 1.0 / 3.0]))
+    assert h[0] == -h[1] and l[0] == -l[1] and h[0] < 0 and l[0] <= 0
