@@ -34,8 +34,11 @@ namespace tdse {
 // restart the forward coefficients at zero (the exact boundary condition of the Thomas sweep),
 // rows at or beyond the far wall restart the back substitution at zero; the own segment is rows
 // K .. K + m - 1.  Observables are summed over the L lanes of an instance by shuffles, then over the
-// warps.  No bulk copies on this path (it serves small batches, where the FP64 elimination is the
-// bound in both precisions); MIXED sums the observables in double directly.
+// warps.  No bulk copies on this path (it serves small batches and the widened groups of uneven
+// batches, where the FP64 elimination is the bound in both precisions).  The observable sums stay
+// off the FP64 pipe as on the 32-wide path: float pairs (FP64) or floats (MIXED) over blocks of
+// kObsBlock own rows, each block widened to double by integer operations; tab_obs is the class's
+// float4 table, (x_hi, x_lo, dV_hi, dV_lo) for FP64 and (x, dV, m, -) for MIXED.
 template <bool kMixed, bool kCkpt>
 __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, typename Prec<kMixed>::C* __restrict__ ps,
                                             const double2* __restrict__ tab_ab2, const double2* __restrict__ tab_xv2,
@@ -45,7 +48,7 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, 
                                             bool initial, const double* __restrict__ E, double* __restrict__ d_out,
                                             double* __restrict__ a_out, int64_t sample_base,
                                             typename Prec<kMixed>::C* __restrict__ sc, double* red, int* status,
-                                            double2* __restrict__ ck, int kc)
+                                            double2* __restrict__ ck, int kc, const float4* __restrict__ tab_obs)
 {
     using R = typename Prec<kMixed>::R;
     using Cx = typename Prec<kMixed>::C;
@@ -146,6 +149,20 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, 
         ObsSums o{0.0, 0.0, 0.0};
         {
             R Yr = 0, Yi = 0;
+            float snh = 0.f, snl = 0.f, sxh = 0.f, sxl = 0.f, svh = 0.f, svl = 0.f;
+            int blk = 0;
+            auto fold = [&]() {
+                o.n = F.add(f2d_int(snh), o.n);
+                o.x = F.add(f2d_int(sxh), o.x);
+                o.v = F.add(f2d_int(svh), o.v);
+                if constexpr (!kMixed) {
+                    o.n = F.add(f2d_int(snl), o.n);
+                    o.x = F.add(f2d_int(sxl), o.x);
+                    o.v = F.add(f2d_int(svl), o.v);
+                }
+                snh = snl = sxh = sxl = svh = svl = 0.f;
+                blk = 0;
+            };
             const Cx* r = sc + (int64_t)(nrows - 1) * (2 * kLanes);
 #pragma unroll 2
             for (int rr = nrows - 1; rr >= K; --rr) {
@@ -168,13 +185,23 @@ __device__ __forceinline__ void split_slice(const GroupDesc& G, const Fma64& F, 
                         xi = F.mul(xi, mm);
                     }
                     if (active) *pw = mk(xr, xi);
-                    const double rho = fma((double)xr, (double)xr, F.mul((double)xi, (double)xi));
-                    const double2 xv = __ldg(tab_xv2 + j);
-                    o.n = F.add(rho, o.n);
-                    o.x = fma(xv.x, rho, o.x);
-                    o.v = fma(xv.y, rho, o.v);
+                    const float4 tf = __ldg(tab_obs + j);
+                    if constexpr (kMixed) {
+                        const float rho = fmaf(xr, xr, xi * xi);
+                        snh += rho;
+                        sxh = fmaf(tf.x, rho, sxh);
+                        svh = fmaf(tf.y, rho, svh);
+                    } else {
+                        float rh, rl;
+                        sq_mod_ff(xr, xi, rh, rl);
+                        ff_acc(snh, snl, rh, rl);
+                        ff_fma_acc(sxh, sxl, tf.x, tf.y, rh, rl);
+                        ff_fma_acc(svh, svl, tf.z, tf.w, rh, rl);
+                    }
+                    if (++blk == kObsBlock) fold();
                 }
             }
+            fold();
         }
         const ObsSums t = reduce_obs(lane_sum(o), red, P);   // its barrier orders this step's writes
         if (w == 0 && q == 0 && active) {
@@ -287,7 +314,8 @@ k_propagate_full_cn(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         if (G.I != kLanes) {
             split_slice<kMixed, kCkpt>(G, F, ps, tab_ab2, tab_xv2, tab_m, inv_beta, two_over_beta, dx, jm_lo, jm_hi,
                                        nt, row, slot, n0, n1, kslice == 0 && step_begin == 0, E, d_out, a_out,
-                                       sample_base, sc, red, status, kCkpt ? ckpt + ckpt_off[g] : nullptr, kc);
+                                       sample_base, sc, red, status, kCkpt ? ckpt + ckpt_off[g] : nullptr, kc,
+                                       reinterpret_cast<const float4*>(tab + (kMixed ? tab_fx(C) : tab_xff(C))));
         } else {
         if (kslice == 0 && step_begin == 0) {
             // observables of the initial state
