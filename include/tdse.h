@@ -333,10 +333,12 @@ tdse_status tdse_set_layout(tdse_batch* batch, int32_t lanes_per_instance);
 tdse_status tdse_set_launch(tdse_batch* batch, int32_t warps_per_cta, int32_t ctas_per_sm, int32_t slice_steps,
                             int32_t max_ctas);
 
-/* The layout (lanes per instance) that the cost model of tdse_set_layout would pick for a batch of
- * these instances on a GPU with sm_count SMs, computed on the host without a GPU and without
- * creating anything: the planning step of tdse_batch_create on its own, for capacity planning and
- * tests.  The paper has no counterpart.  Arguments as tdse_batch_create; *lanes_out receives L. */
+/* The layout (lanes per instance) that the per-step cost model of tdse_set_layout would pick for a
+ * batch of these instances on a GPU with sm_count SMs, computed on the host without a GPU and
+ * without creating anything, for capacity planning and tests.  It takes no step counts: when the
+ * instances' Nt differ, tdse_batch_create may also widen the longest groups beyond this L so that
+ * no group outlasts the rest of the batch (tdse_plan reports the widest).  The paper has no
+ * counterpart.  Arguments as tdse_batch_create; *lanes_out receives L. */
 tdse_status tdse_model_layout(const tdse_instance* inst_host, int64_t n_inst, double dt, tdse_precision precision,
                               tdse_scheme scheme, int32_t sm_count, int32_t* lanes_out);
 
