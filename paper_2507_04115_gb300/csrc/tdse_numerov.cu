@@ -22,7 +22,10 @@ namespace tdse {
 // sigma m - K + r, rows before the first wall restart the forward recurrence at zero and rows at or
 // beyond the far wall restart the back substitution, so all lanes run the same trip counts.  The
 // own segment is rows K .. K + m - 1; the phase rotation is re-seeded at its first point.
-// Observables are summed over the L lanes by shuffles, then over the warps, in double.
+// Observables are kept off the FP64 pipe as on the 32-wide path (float pairs in FP64, floats in
+// MIXED, widened to double every kObsBlock own rows; tab_obs is the class's float4 table,
+// (x_hi, x_lo, dV_hi, dV_lo) for FP64 and (x, dV, m, -) for MIXED), then summed over the L lanes
+// by shuffles and over the warps in double.
 template <bool kMixed>
 __device__ __forceinline__ void numerov_split_slice(
     const GroupDesc& G, const ClassDesc& C, const Fma64& F, typename Prec<kMixed>::C* __restrict__ ps,
@@ -30,7 +33,7 @@ __device__ __forceinline__ void numerov_split_slice(
     const float2* __restrict__ tF, const double2* __restrict__ tab_xv2, const double* __restrict__ tab_m, int jm_lo,
     int jm_hi, int64_t nt, int64_t row, int64_t slot, int64_t n0, int64_t n1, bool initial, double dt,
     const double* __restrict__ E, double* __restrict__ d_out, double* __restrict__ a_out, int64_t sample_base,
-    typename Prec<kMixed>::C* __restrict__ sc, double* red, int* status)
+    typename Prec<kMixed>::C* __restrict__ sc, double* red, int* status, const float4* __restrict__ tab_obs)
 {
     using R = typename Prec<kMixed>::R;
     using Cx = typename Prec<kMixed>::C;
@@ -130,6 +133,20 @@ __device__ __forceinline__ void numerov_split_slice(
             const int reseed = kMixed ? 8 : 64;
             int own_count = 0;
             R yr = 0, yi = 0;
+            float snh = 0.f, snl = 0.f, sxh = 0.f, sxl = 0.f, svh = 0.f, svl = 0.f;
+            int blk = 0;
+            auto fold = [&]() {
+                o.n = F.add(f2d_int(snh), o.n);
+                o.x = F.add(f2d_int(sxh), o.x);
+                o.v = F.add(f2d_int(svh), o.v);
+                if constexpr (!kMixed) {
+                    o.n = F.add(f2d_int(snl), o.n);
+                    o.x = F.add(f2d_int(sxl), o.x);
+                    o.v = F.add(f2d_int(svl), o.v);
+                }
+                snh = snl = sxh = sxl = svh = svl = 0.f;
+                blk = 0;
+            };
             const Cx* r = sc + (int64_t)(nrows - 1) * (2 * kLanes);
             for (int rr = nrows - 1; rr >= K; --rr) {
                 const int j = base + rr;
@@ -162,19 +179,34 @@ __device__ __forceinline__ void numerov_split_slice(
                     const R qr = fma(phr, wr_, F.mul(-phi, wi_));   // next point: x smaller by dx
                     phi = fma(phr, wi_, F.mul(phi, wr_));
                     phr = qr;
-                    if (j < jm_lo || j > jm_hi) {
-                        const R mm = (R)__ldg(tab_m + j);
-                        xr = F.mul(xr, mm);
-                        xi = F.mul(xi, mm);
+                    const float4 tf = __ldg(tab_obs + j);
+                    if constexpr (kMixed) {
+                        if (j < jm_lo || j > jm_hi) {
+                            xr *= tf.z;
+                            xi *= tf.z;
+                        }
+                        if (active) *pw = mk(xr, xi);
+                        const float rho = fmaf(xr, xr, xi * xi);
+                        snh += rho;
+                        sxh = fmaf(tf.x, rho, sxh);
+                        svh = fmaf(tf.y, rho, svh);
+                    } else {
+                        if (j < jm_lo || j > jm_hi) {
+                            const R mm = __ldg(tab_m + j);
+                            xr = F.mul(xr, mm);
+                            xi = F.mul(xi, mm);
+                        }
+                        if (active) *pw = mk(xr, xi);
+                        float rh, rl;
+                        sq_mod_ff(xr, xi, rh, rl);
+                        ff_acc(snh, snl, rh, rl);
+                        ff_fma_acc(sxh, sxl, tf.x, tf.y, rh, rl);
+                        ff_fma_acc(svh, svl, tf.z, tf.w, rh, rl);
                     }
-                    if (active) *pw = mk(xr, xi);
-                    const double rho = fma((double)xr, (double)xr, F.mul((double)xi, (double)xi));
-                    const double2 xv = __ldg(tab_xv2 + j);
-                    o.n = F.add(rho, o.n);
-                    o.x = fma(xv.x, rho, o.x);
-                    o.v = fma(xv.y, rho, o.v);
+                    if (++blk == kObsBlock) fold();
                 }
             }
+            fold();
         }
         const ObsSums t = reduce_obs(lane_sum(o), red, P);   // its barrier orders this step's writes
         if (w == 0 && q == 0 && active) {
@@ -242,6 +274,7 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         const double2* __restrict__ tC = reinterpret_cast<const double2*>(tab + tab_nc(C));
         const float2* __restrict__ tF = reinterpret_cast<const float2*>(tab + tab_nf(C));
         const float4* __restrict__ tab_f4 = reinterpret_cast<const float4*>(tab + tab_fx(C));
+        const float4* __restrict__ tab_xff4 = reinterpret_cast<const float4*>(tab + tab_xff(C));
         const int jm_lo = mask_on ? C.jm_lo : 0;
         const int jm_hi = mask_on ? C.jm_hi : N - 1;
         const int64_t n_end = min(step_end, G.nt_max);
@@ -252,7 +285,7 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
         if (G.I != kLanes) {
             numerov_split_slice<kMixed>(G, C, F, ps, tW, tL, tC, tF, tab_xv2, tab_m, jm_lo, jm_hi, nt, row, slot, n0,
                                         n1, kslice == 0 && step_begin == 0, dt, E, d_out, a_out, sample_base, sc, red,
-                                        status);
+                                        status, kMixed ? tab_f4 : tab_xff4);
         } else {
         if (kslice == 0 && step_begin == 0) {
             ObsSums o{0.0, 0.0, 0.0};
@@ -354,8 +387,22 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                 }
                 R phr = 1, phi = 0;
                 const int reseed = kMixed ? 8 : 64;
-                R fn = 0, fx = 0, fv = 0;
+                // observable sums off the FP64 pipe: float pairs (FP64) or floats (MIXED) over blocks
+                // of kObsBlock points, each block widened to double by integer operations
+                float snh = 0.f, snl = 0.f, sxh = 0.f, sxl = 0.f, svh = 0.f, svl = 0.f;
                 int blk = 0;
+                auto fold = [&]() {
+                    o.n = F.add(f2d_int(snh), o.n);
+                    o.x = F.add(f2d_int(sxh), o.x);
+                    o.v = F.add(f2d_int(svh), o.v);
+                    if constexpr (!kMixed) {
+                        o.n = F.add(f2d_int(snl), o.n);
+                        o.x = F.add(f2d_int(sxl), o.x);
+                        o.v = F.add(f2d_int(svl), o.v);
+                    }
+                    snh = snl = sxh = sxl = svh = svl = 0.f;
+                    blk = 0;
+                };
                 for (int j = e - 1; j >= s; --j) {
                     const Cx d2 = r[lane];
                     r -= 2 * kLanes;
@@ -395,17 +442,10 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                             xi *= fxv.z;
                         }
                         if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
-                        const R rho = fma(xr, xr, xi * xi);
-                        fn += rho;
-                        fx = fma(fxv.x, rho, fx);
-                        fv = fma(fxv.y, rho, fv);
-                        if (++blk == 8) {
-                            o.n += (double)fn;
-                            o.x += (double)fx;
-                            o.v += (double)fv;
-                            fn = fx = fv = 0;
-                            blk = 0;
-                        }
+                        const float rho = fmaf(xr, xr, xi * xi);
+                        snh += rho;
+                        sxh = fmaf(fxv.x, rho, sxh);
+                        svh = fmaf(fxv.y, rho, svh);
                     } else {
                         if (j < jm_lo || j > jm_hi) {
                             const R mm = __ldg(tab_m + j);
@@ -413,18 +453,16 @@ k_propagate_numerov(const GroupDesc* __restrict__ groups, int64_t n_groups, cons
                             xi = F.mul(xi, mm);
                         }
                         if (active) ps[(int64_t)j * kLanes + lane] = mk(xr, xi);
-                        const R rho = fma(xr, xr, F.mul(xi, xi));
-                        const double2 xv = __ldg(tab_xv2 + j);
-                        o.n = F.add(rho, o.n);
-                        o.x = fma(xv.x, rho, o.x);
-                        o.v = fma(xv.y, rho, o.v);
+                        float rh, rl;
+                        sq_mod_ff(xr, xi, rh, rl);
+                        const float4 xf = __ldg(tab_xff4 + j);   // (x_hi, x_lo, dV_hi, dV_lo)
+                        ff_acc(snh, snl, rh, rl);
+                        ff_fma_acc(sxh, sxl, xf.x, xf.y, rh, rl);
+                        ff_fma_acc(svh, svl, xf.z, xf.w, rh, rl);
                     }
+                    if (++blk == kObsBlock) fold();
                 }
-                if constexpr (kMixed) {
-                    o.n += (double)fn;
-                    o.x += (double)fx;
-                    o.v += (double)fv;
-                }
+                fold();
             }
             const ObsSums t = reduce_obs(o, red, P);
             if (w == 0 && active) {
