@@ -151,8 +151,11 @@ __global__ void k_ed_solve(const GroupDesc* __restrict__ groups, const ClassDesc
             pc = pn;
             pn = j + 2 < N ? ps[(int64_t)(j + 2) * I] : Cx{0, 0};
         }
-        // backward: y_j = d'_j - c'_j y_{j+1}, sum |y|^2
+        // backward: y_j = d'_j - c'_j y_{j+1}, sum |y|^2 (|y|^2 and the sum as float pairs on the FP32
+        // pipe, widened to double every kObsBlock points, as the propagation kernels' observables)
         double yr = 0.0, yi = 0.0, s = 0.0;
+        float sh = 0.f, sl = 0.f;
+        int blk = 0;
         double2 da = sc[(int64_t)(N - 1) * kLanes + lane], ca = Cp[(int64_t)(N - 1) * nE_pad];
         double2 db = make_double2(0.0, 0.0), cb = db;
         if (N > 1) {
@@ -170,8 +173,16 @@ __global__ void k_ed_solve(const GroupDesc* __restrict__ groups, const ClassDesc
             const double nr = fma(-cp.x, yr, fma(cp.y, yi, d2.x));
             yi = fma(-cp.x, yi, fma(-cp.y, yr, d2.y));
             yr = nr;
-            s = fma(yr, yr, fma(yi, yi, s));
+            float rh, rl;
+            sq_mod_ff(yr, yi, rh, rl);
+            ff_acc(sh, sl, rh, rl);
+            if (++blk == kObsBlock) {
+                s = F.add(f2d_int(sh), F.add(f2d_int(sl), s));
+                sh = sl = 0.f;
+                blk = 0;
+            }
         }
+        s = F.add(f2d_int(sh), F.add(f2d_int(sl), s));
         if (k < nE) P_out[inst * (int64_t)nE + k] = (eps / 3.14159265358979323846) * s * C.dx;
     }
 }
