@@ -58,9 +58,12 @@ typedef enum {
 } tdse_status;
 
 typedef enum {
-    TDSE_FP64 = 0,   /* all arithmetic and storage in IEEE double */
+    TDSE_FP64 = 0,   /* the solve and the wavefunctions in IEEE double; |psi|^2 and the observable
+                        sums as float pairs (about 2^-44 relative per point) over blocks of 16
+                        points, added in double across blocks */
     TDSE_MIXED = 1   /* psi, the solve's right-hand side and back substitution in float; the
-                        elimination recurrence (pivots) and the observable sums in double */
+                        elimination recurrence (pivots) in double; the observables as float
+                        partial sums over 16 points, added in double across blocks */
 } tdse_precision;
 
 typedef enum {
