@@ -117,3 +117,43 @@ def test_squared_modulus_pair_bound():
     # the signed split keeps the sign on both parts
     h, l = _split_signed(np.array([-1.0 / 3.0, 1.0 / 3.0]))
     assert h[0] == -h[1] and l[0] == -l[1] and h[0] < 0 and l[0] <= 0
+
+
+def _ff_acc(sh, sl, ah, al):
+    """The kernels' float-pair accumulation step (two-sum, then a fast two-sum renormalisation)."""
+    f = np.float32
+    t = f(sh + ah)
+    bp = f(t - sh)
+    err = f(f(sh - f(t - bp)) + f(ah - bp))
+    lo = f(sl + f(err + al))
+    nh = f(t + lo)
+    return nh, f(lo - f(nh - t))
+
+
+def _ff_fma_acc(sh, sl, xh, xl, rh, rl):
+    f = np.float32
+    p = f(xh * rh)
+    e = f(np.float64(xh) * np.float64(rh) - np.float64(p))   # the FMA residual, exact
+    lo = f(np.float64(xh) * np.float64(rl) + np.float64(f(np.float64(xl) * np.float64(rh) + np.float64(e))))
+    return _ff_acc(sh, sl, p, lo)
+
+
+def test_block_sums_of_float_pairs():
+    """A block of 16 terms x_j rho_j summed as the kernels do (x and rho as float pairs) stays within
+    2^-44 of the exact sum relative to the sum of magnitudes, for terms of mixed sign."""
+    rng = np.random.default_rng(20)
+    worst = 0.0
+    for _ in range(3000):
+        rho = np.abs(rng.standard_normal(16)) * np.exp(rng.uniform(-20, 2))
+        x = rng.uniform(-300, 300, 16)
+        rh, rl = _split(rho)
+        xh = x.astype(np.float32)
+        xl = (x - xh.astype(np.float64)).astype(np.float32)
+        sh, sl = np.float32(0), np.float32(0)
+        for j in range(16):
+            sh, sl = _ff_fma_acc(sh, sl, xh[j], xl[j], rh[j], rl[j])
+        got = np.float64(sh) + np.float64(sl)
+        exact = float(np.sum(x.astype(np.longdouble) * rho.astype(np.longdouble)))
+        worst = max(worst, abs(got - exact) / float(np.sum(np.abs(x * rho))))
+    assert worst < 2.0 ** -44
+    assert worst > 2.0 ** -60      # not exact: the comparison can fail
